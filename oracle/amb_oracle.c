@@ -1,0 +1,374 @@
+/*
+ * amb_oracle.c -- plain, slow, single-threaded CPU statement of the AMBER
+ * per-step population update (wealth transfer, random walk on a torus grid,
+ * spatial SIR on a grid), used as the parity oracle.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call this code:
+ * only tests/, __graft_entry__.smoke() and the cpu_baseline / reference legs
+ * of bench.py load it.  It shares no source with the CUDA library (its own
+ * Philox, its own threshold tables, its own index and statistics).
+ *
+ * Every loop runs over agents in id order on plain arrays.  Synchronous
+ * (snapshot-then-apply) semantics throughout (paper Sec. 3.4): every agent
+ * reads the state as it was at the start of the step.
+ *
+ * Readings of the paper where it is silent are listed in the design doc; the ones
+ * this file implements are restated next to the code that implements them.
+ *
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -shared -fPIC (oracle/build.py).
+ * -ffp-contract=off matters: the threshold tables are defined by individual
+ * IEEE-754 double operations and must not be fused into FMAs.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL 1
+#define ORC_ENOMEM 2
+
+#define ST_S 0
+#define ST_I 1
+#define ST_R 2
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as  */
+/* easy as 1, 2, 3", SC'11).  Written from the published round function:    */
+/* two 32x32->64 products per round, the high halves xor-ed with the other  */
+/* two words and the round key, the key bumped by the Weyl constants        */
+/* between rounds, ten rounds.                                              */
+/* ------------------------------------------------------------------------ */
+static const uint32_t PH_MUL_A = 0xD2511F53u; /* multiplies word 0 */
+static const uint32_t PH_MUL_B = 0xCD9E8D57u; /* multiplies word 2 */
+static const uint32_t PH_WEYL_0 = 0x9E3779B9u; /* golden ratio */
+static const uint32_t PH_WEYL_1 = 0xBB67AE85u; /* sqrt(3) - 1 */
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t w0 = ctr[0], w1 = ctr[1], w2 = ctr[2], w3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        uint64_t pa = (uint64_t)PH_MUL_A * (uint64_t)w0;
+        uint64_t pb = (uint64_t)PH_MUL_B * (uint64_t)w2;
+        uint32_t n0 = (uint32_t)(pb >> 32) ^ w1 ^ k0;
+        uint32_t n1 = (uint32_t)pb;
+        uint32_t n2 = (uint32_t)(pa >> 32) ^ w3 ^ k1;
+        uint32_t n3 = (uint32_t)pa;
+        w0 = n0; w1 = n1; w2 = n2; w3 = n3;
+        k0 += PH_WEYL_0;
+        k1 += PH_WEYL_1;
+    }
+    out[0] = w0; out[1] = w1; out[2] = w2; out[3] = w3;
+}
+
+/* The draw of one agent at one step: key = (seed, replicate), counter =
+ * (agent id, step, 0, 0).  Initial positions use step = 0xFFFFFFFF. */
+static void draw(uint32_t seed, uint32_t rep, uint32_t id, uint32_t step, uint32_t u[4])
+{
+    uint32_t c[4] = {id, step, 0u, 0u};
+    uint32_t k[2] = {seed, rep};
+    orc_philox4x32_10(c, k, u);
+}
+
+#define INIT_STEP 0xFFFFFFFFu
+
+/* Uniform integer in [0, n): the high word of u * n (no rejection). */
+static uint32_t uniform_below(uint32_t u, uint32_t n)
+{
+    return (uint32_t)(((uint64_t)u * (uint64_t)n) >> 32);
+}
+
+/* Moore neighbourhood, direction d = top three bits of the move word. */
+static const int MOORE_DX[8] = {-1, 0, 1, -1, 1, -1, 0, 1};
+static const int MOORE_DY[8] = {-1, -1, -1, 0, 0, 1, 1, 1};
+
+/* Non-negative residue of (v + d) on a ring of L sites, v in [0, L). */
+static int32_t wrap_add(int32_t v, int d, uint32_t L)
+{
+    int64_t s = (int64_t)v + d;
+    int64_t m = (int64_t)L;
+    s %= m;
+    if (s < 0) s += m;
+    return (int32_t)s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Initialisation (paper Sec. 3.3, add_agents: one call creates n agents).  */
+/* ------------------------------------------------------------------------ */
+void orc_init_wealth(uint32_t n, int32_t w_init, int32_t *w)
+{
+    for (uint32_t i = 0; i < n; ++i) w[i] = w_init;
+}
+
+/* Positions uniform on the L x L torus: x from word 0, y from word 1 of the
+ * agent's initial draw. */
+void orc_init_positions(uint32_t n, uint32_t L, uint32_t seed, uint32_t rep,
+                        int32_t *x, int32_t *y)
+{
+    for (uint32_t i = 0; i < n; ++i) {
+        uint32_t u[4];
+        draw(seed, rep, i, INIT_STEP, u);
+        x[i] = (int32_t)uniform_below(u[0], L);
+        y[i] = (int32_t)uniform_below(u[1], L);
+    }
+}
+
+/* Initial infected: agents 0 .. n0-1 (their positions are independent
+ * uniform draws, so they form a uniformly random spatial sample); the count
+ * equals the configured parameter exactly (paper Sec. 5.1.3). */
+void orc_init_sir_state(uint32_t n, uint32_t n0, uint8_t *state)
+{
+    for (uint32_t i = 0; i < n; ++i) state[i] = (i < n0) ? ST_I : ST_S;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Wealth transfer (paper Sec. 5.1.2; Listings 2-3).                        */
+/* Every agent with positive wealth (on the snapshot) gives one unit to a   */
+/* uniformly chosen OTHER agent: r' = uniform_below(u0, n-1), r = r' + (r'  */
+/* >= i).  Duplicate recipients accumulate (scatter_add).  n == 1: no agent */
+/* has another agent to give to, so nothing happens.                        */
+/* counts[0] = donors this step, counts[1] = total wealth after the step.   */
+/* Arithmetic on wealth wraps modulo 2^32.                                  */
+/* ------------------------------------------------------------------------ */
+int orc_wealth_step(uint32_t n, uint32_t seed, uint32_t rep, uint32_t t,
+                    int32_t *w, int64_t counts[4])
+{
+    counts[0] = counts[1] = counts[2] = counts[3] = 0;
+    if (n >= 2) {
+        int32_t *snap = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+        if (!snap) return ORC_ENOMEM;
+        memcpy(snap, w, sizeof(int32_t) * (size_t)n);
+        for (uint32_t i = 0; i < n; ++i) {
+            if (snap[i] > 0) {
+                uint32_t u[4];
+                draw(seed, rep, i, t, u);
+                uint32_t r = uniform_below(u[0], n - 1);
+                if (r >= i) r += 1;
+                w[i] = (int32_t)((uint32_t)w[i] - 1u);
+                w[r] = (int32_t)((uint32_t)w[r] + 1u);
+                counts[0] += 1;
+            }
+        }
+        free(snap);
+    }
+    for (uint32_t i = 0; i < n; ++i) counts[1] += w[i];
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Random walk (paper Sec. 5.1.2, re-cast on an integer torus): every agent */
+/* steps to one of its 8 Moore neighbours, direction = u0 >> 29.            */
+/* ------------------------------------------------------------------------ */
+int orc_walk_step(uint32_t n, uint32_t L, uint32_t seed, uint32_t rep, uint32_t t,
+                  int32_t *x, int32_t *y)
+{
+    if (L == 0) return ORC_EINVAL;
+    for (uint32_t i = 0; i < n; ++i) {
+        uint32_t u[4];
+        draw(seed, rep, i, t, u);
+        uint32_t d = u[0] >> 29;
+        x[i] = wrap_add(x[i], MOORE_DX[d], L);
+        y[i] = wrap_add(y[i], MOORE_DY[d], L);
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* SIR probabilities as uint32 thresholds; an event with probability p      */
+/* happens iff the uniform word u < T(p), T(p) = min(floor(p 2^32), 2^32-1).*/
+/* Infection with k infected cell-mates: p_k = 1 - (1-beta)^k, where        */
+/* (1-beta)^k is built by k successive IEEE double products (no pow()).     */
+/* t_inf[0] = 0.  The table ends at K: the first k whose entry is the       */
+/* largest uint32, or after which the power no longer changes, or k = cap;  */
+/* every entry beyond K equals t_inf[K], so lookups use min(k, K).          */
+/* ------------------------------------------------------------------------ */
+static uint32_t prob_to_threshold(double p)
+{
+    double v = p * 4294967296.0; /* exact scaling by 2^32 */
+    if (!(v > 0.0)) return 0u;
+    if (v >= 4294967295.0) return 0xFFFFFFFFu;
+    return (uint32_t)v; /* truncation == floor for v >= 0 */
+}
+
+int orc_sir_thresholds(double beta, double gamma, uint32_t cap,
+                       uint32_t *t_inf, uint32_t *K_out, uint32_t *t_rec)
+{
+    if (!(beta >= 0.0 && beta <= 1.0) || !(gamma >= 0.0 && gamma <= 1.0)) return ORC_EINVAL;
+    if (cap < 1) cap = 1;
+    double keep = 1.0 - beta; /* survival factor for one infected cell-mate */
+    double q = 1.0;           /* probability of escaping k infected */
+    t_inf[0] = 0u;
+    uint32_t K = cap;
+    for (uint32_t k = 1; k <= cap; ++k) {
+        double q_next = q * keep;
+        double p = 1.0 - q_next;
+        t_inf[k] = prob_to_threshold(p);
+        if (t_inf[k] == 0xFFFFFFFFu) { K = k; break; }
+        if (q_next == q) { K = (k > 1) ? k - 1 : 1; break; }
+        q = q_next;
+    }
+    *K_out = K;
+    *t_rec = prob_to_threshold(gamma);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Spatial SIR on the grid (paper Sec. 5.1.2, re-cast with same-cell         */
+/* contacts).  One step t:                                                   */
+/*  1. every agent (S, I and R) makes its Moore move as in the random walk;  */
+/*  2. with the states of the start of the step, k[c] = number of infected   */
+/*     agents whose NEW cell is c;                                           */
+/*  3. S agent in cell c with k[c] >= 1 becomes I iff u1 < t_inf[min(k,K)];  */
+/*     I agent (start-of-step state) becomes R iff u2 < t_rec; R stays R.    */
+/*     An agent infected in this step does not recover in this step.        */
+/* counts = {S, I, R, new infections} after the step.                       */
+/* ------------------------------------------------------------------------ */
+int orc_sir_step(uint32_t n, uint32_t L, uint32_t seed, uint32_t rep, uint32_t t,
+                 const uint32_t *t_inf, uint32_t K, uint32_t t_rec,
+                 int32_t *x, int32_t *y, uint8_t *state, int64_t counts[4])
+{
+    if (L == 0) return ORC_EINVAL;
+    uint64_t C = (uint64_t)L * (uint64_t)L;
+    uint32_t *u1 = (uint32_t *)malloc(sizeof(uint32_t) * ((size_t)n + 1));
+    uint32_t *u2 = (uint32_t *)malloc(sizeof(uint32_t) * ((size_t)n + 1));
+    uint32_t *kc = (uint32_t *)calloc((size_t)C, sizeof(uint32_t));
+    if (!u1 || !u2 || !kc) { free(u1); free(u2); free(kc); return ORC_ENOMEM; }
+
+    /* 1. moves */
+    for (uint32_t i = 0; i < n; ++i) {
+        uint32_t u[4];
+        draw(seed, rep, i, t, u);
+        uint32_t d = u[0] >> 29;
+        x[i] = wrap_add(x[i], MOORE_DX[d], L);
+        y[i] = wrap_add(y[i], MOORE_DY[d], L);
+        u1[i] = u[1];
+        u2[i] = u[2];
+    }
+    /* 2. infected per new cell, start-of-step states */
+    for (uint32_t i = 0; i < n; ++i)
+        if (state[i] == ST_I) kc[(uint64_t)y[i] * L + (uint64_t)x[i]] += 1;
+    /* 3. transitions against the snapshot */
+    int64_t newinf = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        uint8_t s = state[i];
+        if (s == ST_S) {
+            uint32_t k = kc[(uint64_t)y[i] * L + (uint64_t)x[i]];
+            if (k >= 1) {
+                uint32_t kk = (k < K) ? k : K;
+                if (u1[i] < t_inf[kk]) { state[i] = ST_I; newinf += 1; }
+            }
+        } else if (s == ST_I) {
+            if (u2[i] < t_rec) state[i] = ST_R;
+        }
+    }
+    counts[0] = counts[1] = counts[2] = 0;
+    for (uint32_t i = 0; i < n; ++i) counts[state[i]] += 1; /* states are 0, 1, 2 */
+    counts[3] = newinf;
+    free(u1); free(u2); free(kc);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Counting-sort cell index (paper Sec. 4.1, grid environment): cell id     */
+/* c = y * L + x; start[c] = number of agents in cells < c; start[C] = n;   */
+/* perm lists agent ids cell by cell, ascending id inside a cell (a stable  */
+/* counting sort).                                                          */
+/* ------------------------------------------------------------------------ */
+int orc_cell_index(uint32_t n, uint32_t L, const int32_t *x, const int32_t *y,
+                   int64_t *start, int32_t *perm)
+{
+    if (L == 0) return ORC_EINVAL;
+    uint64_t C = (uint64_t)L * (uint64_t)L;
+    int64_t *cursor = (int64_t *)calloc((size_t)C, sizeof(int64_t));
+    if (!cursor) return ORC_ENOMEM;
+    for (uint64_t c = 0; c <= C; ++c) start[c] = 0;
+    for (uint32_t i = 0; i < n; ++i) start[(uint64_t)y[i] * L + (uint64_t)x[i] + 1] += 1;
+    for (uint64_t c = 0; c < C; ++c) start[c + 1] += start[c];
+    for (uint32_t i = 0; i < n; ++i) {
+        uint64_t c = (uint64_t)y[i] * L + (uint64_t)x[i];
+        perm[start[c] + cursor[c]] = (int32_t)i;
+        cursor[c] += 1;
+    }
+    free(cursor);
+    return ORC_OK;
+}
+
+/* Occupancy per cell (occ[C]) and the histogram of occupancies
+ * (hist[m] = number of cells holding m agents, m < hist_len). */
+int orc_occupancy(uint32_t n, uint32_t L, const int32_t *x, const int32_t *y,
+                  int32_t *occ, int64_t *hist, uint32_t hist_len)
+{
+    if (L == 0) return ORC_EINVAL;
+    uint64_t C = (uint64_t)L * (uint64_t)L;
+    for (uint64_t c = 0; c < C; ++c) occ[c] = 0;
+    for (uint32_t i = 0; i < n; ++i) occ[(uint64_t)y[i] * L + (uint64_t)x[i]] += 1;
+    for (uint32_t m = 0; m < hist_len; ++m) hist[m] = 0;
+    for (uint64_t c = 0; c < C; ++c)
+        if ((uint32_t)occ[c] < hist_len) hist[occ[c]] += 1;
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gini coefficient of the wealth column, from the ascending order          */
+/* statistics w_(1) <= ... <= w_(n):                                        */
+/*   G = sum_i (2i - n - 1) w_(i) / (n * sum_i w_i),                         */
+/* numerator and denominator as exact integers, then one double division.   */
+/* sum w == 0 gives G = 0.                                                  */
+/* ------------------------------------------------------------------------ */
+static int cmp_i32(const void *a, const void *b)
+{
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+int orc_gini(uint32_t n, const int32_t *w, double *gini, int64_t *num_hi, uint64_t *num_lo,
+             int64_t *total)
+{
+    int32_t *s = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    if (!s) return ORC_ENOMEM;
+    memcpy(s, w, sizeof(int32_t) * (size_t)n);
+    qsort(s, n, sizeof(int32_t), cmp_i32);
+    __int128 num = 0;
+    int64_t tot = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        int64_t coef = 2 * (int64_t)(i + 1) - (int64_t)n - 1;
+        num += (__int128)coef * (__int128)s[i];
+        tot += s[i];
+    }
+    free(s);
+    __int128 den = (__int128)n * (__int128)tot;
+    *gini = (tot == 0) ? 0.0 : (double)num / (double)den;
+    *num_hi = (int64_t)(num >> 64);
+    *num_lo = (uint64_t)num;
+    *total = tot;
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Epidemic curve moments from the per-step infected series I(1..T):        */
+/* peak, first step reaching the peak, and the mean and variance of t under */
+/* the weights I(t): mean = S1/S0, var = (S0 S2 - S1^2) / S0^2 with         */
+/* S_j = sum_t t^j I(t) as exact integers (one double division each).       */
+/* ------------------------------------------------------------------------ */
+int orc_curve_moments(const int64_t *infected, uint32_t T, int64_t *peak, uint32_t *argmax,
+                      double *mean, double *var)
+{
+    unsigned __int128 s0 = 0, s1 = 0, s2 = 0;
+    int64_t pk = -1;
+    uint32_t am = 0;
+    for (uint32_t j = 0; j < T; ++j) {
+        uint64_t t = (uint64_t)j + 1;
+        uint64_t v = (uint64_t)infected[j];
+        if ((int64_t)v > pk) { pk = (int64_t)v; am = (uint32_t)t; }
+        s0 += v;
+        s1 += (unsigned __int128)v * t;
+        s2 += (unsigned __int128)v * t * t;
+    }
+    *peak = (T == 0) ? 0 : pk;
+    *argmax = am;
+    if (s0 == 0) { *mean = 0.0; *var = 0.0; return ORC_OK; }
+    *mean = (double)s1 / (double)s0;
+    unsigned __int128 a = s0 * s2, b = s1 * s1; /* a >= b by Cauchy-Schwarz */
+    *var = (double)(a - b) / ((double)s0 * (double)s0);
+    return ORC_OK;
+}
