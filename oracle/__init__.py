@@ -150,7 +150,7 @@ class Population:
 
     model: "wealth" | "walk" | "sir".  Per-step counts are recorded in
     ``series`` (one row of 4 int64 per step): wealth {donors, total wealth},
-    SIR {S, I, R, new infections}, walk zeros.
+    SIR {S, I, R, new infections}, walk {agent count}.
     """
 
     def __init__(self, model, n, seed, rep=0, L=1, beta=0.0, gamma=0.0, n0=0, w_init=1):
@@ -190,7 +190,8 @@ class Population:
                 _check(Lb.orc_walk_step(self.n, self.L, self.seed, self.rep, self.t,
                                         _p(self.x, ctypes.c_int32), _p(self.y, ctypes.c_int32)),
                        "walk_step")
-                cnt[:] = 0
+                # the walk's count row is the agent count, which never changes
+                cnt[:] = (self.n, 0, 0, 0)
             else:
                 _check(Lb.orc_sir_step(self.n, self.L, self.seed, self.rep, self.t,
                                        _p(self.t_inf, ctypes.c_uint32), self.K, self.t_rec,
