@@ -1,0 +1,393 @@
+"""Throughput benchmark of the columnar agent-step engine on GB300.
+
+Headline workload (one bench step = one synchronous SIR step of the whole
+population through the C ABI): 10,000,000 agents on a 4096 x 4096 torus,
+10,000 initially infected, beta = 0.05, gamma = 0.02, seed 2 -- the
+spatial-SIR configuration (move, cell-index rebuild, per-cell infected
+counts, infection / recovery, per-step counters).  Also reported on the same
+line: wealth transfer (10,000 agents, 100 steps) and random walk (1,000,000
+agents on a 1000 x 1000 torus, 200 steps).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl amb|reference]
+
+With N > 1 (torchrun, one process per GPU) every rank runs an independent
+replicate (replicate = rank): the populations do not exchange data, so the
+scaling is weak and the value is the sum over ranks of agent-steps divided by
+the slowest rank's time.  --impl reference times the CPU oracle (the plain
+single-threaded statement of the same rules) on the same workload.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SIR_CFG = dict(n=10_000_000, L=4096, beta=0.05, gamma=0.02, n0=10_000, seed=2)
+WEALTH_CFG = dict(n=10_000, seed=0, steps=100)
+WALK_CFG = dict(n=1_000_000, L=1000, seed=1, steps=200)
+L2_BYTES = 129 * 1024 * 1024
+
+
+def sir_bytes_per_agent_step(n, L, path):
+    """Algorithmic HBM bytes of one SIR step per agent for the layout in use.
+
+    band path (cell-ordered records): read + write one 8-byte record per
+    agent (id + packed x/state/next draws), write start[C] once -> 16 + 4 C/N.
+    generic path (id-ordered columns): read/write x, y (16), read state (1) and
+    write it (1), cell-id write + read of cnt/inf/cursor/start/ids per agent and
+    per cell: counted as 18 + 8 (ids write/read) + 8 C / N.
+    """
+    C = L * L
+    if path == "band":
+        return 16.0 + 4.0 * C / n
+    return 18.0 + 8.0 + 8.0 * C / n
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v, device):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(world, v, device):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# --------------------------------------------------------------- GPU arm ----
+def time_sir(amb, torch, steps, warmup, rank, stream):
+    c = SIR_CFG
+    pop = amb.Population("sir", c["n"], seed=c["seed"], rep=rank, L=c["L"], beta=c["beta"], gamma=c["gamma"],
+                         n0=c["n0"], stream=stream)
+    for _ in range(warmup):
+        pop.step(1)
+    pop.synchronize()
+    launches0 = amb.amb_launch_count(pop.handle)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for k in range(steps):
+            amb.amb_step(pop.handle, 1)
+            ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+    total_ms = ev[0].elapsed_time(ev[steps])
+    launches = amb.amb_launch_count(pop.handle) - launches0
+    inv = pop.invariants()
+    # the band path launches exactly one kernel per step
+    path = "band" if launches == steps else "generic"
+    pop.close()
+    return total_ms, per, launches, inv, path
+
+
+def time_model_block(amb, torch, model, cfg, stream, rank):
+    """One amb_step(steps) call of the small models, timed on the stream."""
+    kw = dict(seed=cfg["seed"], rep=rank, stream=stream)
+    if "L" in cfg:
+        kw["L"] = cfg["L"]
+    pop = amb.Population(model, cfg["n"], **kw)
+    # warm-up on a throwaway population so the timed one starts at step 0
+    w = amb.Population(model, cfg["n"], **kw)
+    w.step(cfg["steps"])
+    w.synchronize()
+    w.close()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    amb.amb_step(pop.handle, cfg["steps"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = amb.amb_launch_count(pop.handle)
+    inv = pop.invariants()
+    pop.close()
+    return {"agent_steps_per_s": cfg["n"] * cfg["steps"] / (ms / 1e3), "ms": ms, "n": cfg["n"],
+            "steps": cfg["steps"], "gpu_launches": launches, "invariants_ok": bool(inv["ok"])}
+
+
+def run_e2e(amb, torch, steps, rank, stream):
+    c = SIR_CFG
+    n = c["n"]
+    # the initial columns of this replicate, produced once on the host side of
+    # the API (read back from a scratch population) and kept in pinned memory
+    src = amb.Population("sir", n, seed=c["seed"], rep=rank, L=c["L"], beta=c["beta"], gamma=c["gamma"], n0=c["n0"],
+                         stream=stream)
+    hx = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    hy = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    hs = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+    amb.amb_read_column(src.handle, "x", hx)
+    amb.amb_read_column(src.handle, "y", hy)
+    amb.amb_read_column(src.handle, "state", hs)
+    src.close()
+    pop = amb.Population("sir", n, seed=c["seed"], rep=rank, L=c["L"], beta=c["beta"], gamma=c["gamma"], n0=c["n0"],
+                         stream=stream)
+    out_state = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+    row = torch.zeros((1, 4), dtype=torch.int64).numpy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    amb.amb_write_column(pop.handle, "x", hx)
+    amb.amb_write_column(pop.handle, "y", hy)
+    amb.amb_write_column(pop.handle, "state", hs)
+    for k in range(steps):
+        amb.amb_step(pop.handle, 1)
+        amb.amb_counts_range(pop.handle, k, 1, row)
+    amb.amb_read_column(pop.handle, "state", out_state)
+    t1 = time.perf_counter()
+    pop.close()
+    h2d = 9 * n
+    d2h = 32 * steps + n
+    return {"value": n * steps / (t1 - t0), "unit": "agent-steps/s", "h2d_bytes_per_step": h2d / steps,
+            "d2h_bytes_per_step": d2h / steps, "seconds": t1 - t0}
+
+
+def cpu_baseline(budget_s=15.0):
+    """The oracle as it stands on one host core: the full 10M-agent SIR
+    population, as many whole steps as fit in the budget (at least one)."""
+    import oracle
+    c = SIR_CFG
+    p = oracle.Population("sir", c["n"], seed=c["seed"], L=c["L"], beta=c["beta"], gamma=c["gamma"], n0=c["n0"])
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        p.step(1)
+        done += 1
+        if time.perf_counter() - t0 > budget_s * 0.5 or done >= 50:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": c["n"] * done / dt, "unit": "agent-steps/s", "cores": 1, "kind": "oracle",
+            "sample": "first %d steps of the 10M-agent SIR population (all agents, one thread)" % done}
+
+
+def gpu_arm(args):
+    import torch
+    from paper_2601_16292_gb300 import amb
+    world, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=device)
+    amb.lib()
+
+    # untimed extras first (they are short): small models and e2e
+    wealth = time_model_block(amb, torch, "wealth", WEALTH_CFG, stream, rank)
+    walk = time_model_block(amb, torch, "walk", WALK_CFG, stream, rank)
+
+    sampler = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler.start()
+    total_ms, per, launches, inv, path = time_sir(amb, torch, args.steps, args.warmup, rank, stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    total_ms_max = max_over_ranks(world, total_ms, device)
+    agent_steps = sum_over_ranks(world, float(SIR_CFG["n"]) * args.steps, device)
+    e2e = run_e2e(amb, torch, max(args.steps, 3), rank, stream)
+    e2e_val = sum_over_ranks(world, e2e["value"], device)
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    hbm, peak_kind = load_peaks()
+    n, L = SIR_CFG["n"], SIR_CFG["L"]
+    b_alg = sir_bytes_per_agent_step(n, L, path)
+    per_sorted = sorted(per)
+    step_ms = per_sorted[len(per_sorted) // 2]
+    achieved = b_alg * n / (step_ms / 1e3) / 1e9
+    value = agent_steps / (total_ms_max / 1e3)
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            traffic = json.load(f).get("sir_%s" % path)
+    except Exception:
+        traffic = None
+    line = {
+        "metric": "agent-steps/s (spatial SIR, 10M agents, 4096x4096 torus)",
+        "value": value,
+        "unit": "agent-steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int32/u8",
+        "data": "synthetic (seeded Philox initial state, no dataset)",
+        "config": {"workload": "sir_10M_L4096", "n_agents": n, "grid_side": L, "beta": SIR_CFG["beta"],
+                   "gamma": SIR_CFG["gamma"], "n_init_infected": SIR_CFG["n0"], "seed": SIR_CFG["seed"],
+                   "sir_path": path, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "working set %.0f MB > L2 129 MB (no flush needed)" % (
+                       (b_alg * n) / 1e6)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "peak_kind": peak_kind, "traffic": traffic, "bytes_per_agent_step": b_alg,
+                     "kernel_ms_median": step_ms},
+        "cpu_baseline": cpu_baseline(),
+        "e2e": {"value": e2e_val, "unit": "agent-steps/s", "h2d_bytes_per_step": e2e["h2d_bytes_per_step"],
+                "d2h_bytes_per_step": e2e["d2h_bytes_per_step"]},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "invariants_ok": bool(inv["ok"]),
+        "models": {"wealth_10k_100steps": wealth, "walk_1M_L1000_200steps": walk},
+    }
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------- reference arm ----
+def reference_arm(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    c = SIR_CFG
+    p = oracle.Population("sir", c["n"], seed=c["seed"], L=c["L"], beta=c["beta"], gamma=c["gamma"], n0=c["n0"])
+    # each step is a whole step of the full population; keep the run bounded
+    steps = max(1, min(args.steps, 40))
+    warm = max(0, min(args.warmup, 3))
+    for _ in range(warm):
+        p.step(1)
+    t0 = time.perf_counter()
+    p.step(steps)
+    dt = time.perf_counter() - t0
+    v = c["n"] * steps / dt
+    line = {
+        "impl": "reference",
+        "metric": "agent-steps/s (spatial SIR, 10M agents, 4096x4096 torus)",
+        "value": v,
+        "unit": "agent-steps/s",
+        "n_gpus": world,
+        "steps": steps,
+        "warmup": warm,
+        "ms_per_step": dt * 1e3 / steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int32/u8",
+        "data": "synthetic (seeded Philox initial state, no dataset)",
+        "config": {"workload": "sir_10M_L4096", "n_agents": c["n"], "grid_side": c["L"], "beta": c["beta"],
+                   "gamma": c["gamma"], "n_init_infected": c["n0"], "seed": c["seed"]},
+        "cpu_baseline": {"value": v, "unit": "agent-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": "steps %d..%d of the full 10M-agent population, one thread" % (warm, warm + steps)},
+        "e2e": {"value": v, "unit": "agent-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="amb", choices=["amb", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,232 @@
+/*
+ * amb.h -- C ABI of the GB300 columnar agent-step engine.
+ *
+ * The engine runs the per-step population update that AMBER's view API
+ * lowers to column operations (paper Sec. 3.1-3.4): full-population maps,
+ * predicate-filtered (masked) updates and id-indexed scatter-adds over a
+ * struct-of-arrays agent table, for the paper's three benchmark models
+ * (Sec. 5.1.2): wealth transfer, random walk (on an integer torus grid) and
+ * spatial SIR (same-cell contacts on the grid, with the grid's counting-sort
+ * cell index rebuilt every step, Sec. 4.1).
+ *
+ * Conventions for every call:
+ *  - Every function returns an amb_status and never aborts, traps or exits.
+ *    On failure amb_last_error() returns a message (thread-local, valid until
+ *    the next failing call on the same thread).
+ *  - The library owns all device memory it allocates (stream-ordered, on the
+ *    population's stream) and frees it in amb_destroy.  Callers own every
+ *    buffer they pass; no pointer is kept after a call returns.
+ *  - "on_device" buffers are device pointers of the current CUDA device;
+ *    otherwise host pointers (pinned or pageable).
+ *  - Agents are identified by their id 0..n-1; every column read or written
+ *    through this ABI is in id order, whatever the internal layout.
+ *  - One population per host thread at a time; the server object is
+ *    internally synchronised.
+ *  - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key
+ *    (seed, replicate) and counter (agent id, step, 0, 0); seeds are 32-bit.
+ *    Initial positions use step 0xFFFFFFFF, so at most 2^32 - 2 steps.
+ */
+#ifndef AMB_H
+#define AMB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    AMB_OK = 0,
+    AMB_EINVAL = 1,      /* bad argument; nothing was changed */
+    AMB_ENOMEM = 2,      /* device or host allocation failed */
+    AMB_ECUDA = 3,       /* a CUDA call failed (message has the CUDA error) */
+    AMB_EINVARIANT = 4,  /* an invariant check failed (see the report) */
+    AMB_ETIMEOUT = 5,    /* a bounded device-side wait ran out; results invalid */
+    AMB_EBUSY = 6,       /* server: job not finished yet */
+    AMB_EBUDGET = 7,     /* server: job can never fit in the HBM budget */
+    AMB_ENOTFOUND = 8    /* server: unknown ticket */
+} amb_status;
+
+typedef enum { AMB_WEALTH = 0, AMB_WALK = 1, AMB_SIR = 2 } amb_model;
+
+typedef enum {
+    AMB_COL_WEALTH = 0, /* int32, wealth model */
+    AMB_COL_X = 1,      /* int32 in [0, L), walk and SIR */
+    AMB_COL_Y = 2,      /* int32 in [0, L), walk and SIR */
+    AMB_COL_STATE = 3   /* uint8: AMB_S, AMB_I or AMB_R, SIR */
+} amb_col;
+
+enum { AMB_S = 0, AMB_I = 1, AMB_R = 2 };
+
+/* Execution path of the SIR step (amb_params.variant). */
+enum {
+    AMB_SIR_AUTO = 0,    /* band path when the grid allows it, else generic */
+    AMB_SIR_GENERIC = 1, /* id-ordered columns, global counting sort each step */
+    AMB_SIR_BAND = 2     /* cell-ordered records, one fused kernel per step */
+};
+
+typedef struct {
+    uint32_t n;               /* number of agents (0 allowed) */
+    uint32_t grid_side;       /* L: the grid is L x L cells (walk, SIR); >= 1 */
+    double beta;              /* SIR: per infected cell-mate infection probability, [0,1] */
+    double gamma;             /* SIR: per-step recovery probability, [0,1] */
+    uint32_t n_init_infected; /* SIR: agents 0 .. n0-1 start infected (n0 <= n) */
+    int32_t w_init;           /* wealth: initial wealth of every agent */
+    uint32_t variant;         /* SIR execution path, AMB_SIR_*; 0 = automatic */
+} amb_params;
+
+typedef struct amb_pop amb_pop;
+
+/*
+ * Create a population of p->n agents (paper Sec. 3.3, add_agents: one call
+ * creates all agents column by column).  Wealth: every agent holds w_init.
+ * Walk / SIR: positions uniform on the torus, x = hi32(u0 * L),
+ * y = hi32(u1 * L) with u = Philox(key, (id, 0xFFFFFFFF, 0, 0)); SIR: agents
+ * 0 .. n0-1 infected, the rest susceptible.  cuda_stream (a cudaStream_t, may
+ * be NULL for the legacy default stream) orders every later operation on the
+ * population.  Grid limits: walk L <= 2^31 - 1; SIR L <= 46340 (L*L < 2^31).
+ * seed must be < 2^32.  On success *out owns device memory until
+ * amb_destroy.
+ */
+amb_status amb_create(amb_model model, const amb_params *p, uint64_t seed, uint32_t replicate,
+                      void *cuda_stream, amb_pop **out);
+
+/* Free everything the population owns (stream-ordered), then synchronise. */
+amb_status amb_destroy(amb_pop *pop);
+
+/*
+ * Advance k synchronous steps (paper Sec. 3.4: every agent reads the state
+ * of the start of the step).  Asynchronous on the population's stream.
+ *  wealth (Sec. 5.1.2, Listings 2-3): donors = agents with wealth > 0; each
+ *    gives one unit to r = r' + (r' >= id), r' = hi32(u0 * (n-1)); credits
+ *    from several donors add up.  n == 1: nothing happens.
+ *  walk: direction d = u0 >> 29 selects one of the 8 Moore neighbours
+ *    (dx,dy) = (-1,-1) (0,-1) (1,-1) (-1,0) (1,0) (-1,1) (0,1) (1,1); coordinates
+ *    wrap on the torus.
+ *  SIR: every agent moves as in the walk; k = number of agents infected at
+ *    the start of the step whose new cell is the same; a susceptible agent
+ *    becomes infected iff k >= 1 and u1 < T_inf[min(k, K)]; an agent infected
+ *    at the start of the step recovers iff u2 < T_rec; the cell index is
+ *    rebuilt for the new positions.
+ * Per-step counts are recorded on the device (amb_counts).
+ */
+amb_status amb_step(amb_pop *pop, uint32_t k);
+
+/* Overwrite one column with n == p->n values in id order (host or device).
+ * SIR states must be 0, 1 or 2 and positions in [0, L) (checked on the device;
+ * violations return AMB_EINVAL and leave the population unchanged). */
+amb_status amb_write_column(amb_pop *pop, amb_col col, const void *src, size_t n, int src_on_device);
+
+/* Copy one column (id order) into dst (n == p->n elements).  Synchronises the
+ * population's stream; reports a device-side error raised by earlier steps. */
+amb_status amb_read_column(amb_pop *pop, amb_col col, void *dst, size_t n, int dst_on_device);
+
+/*
+ * Per-step counts, 4 int64 per step, rows 0 .. steps-1 (host buffer):
+ *   wealth {donors, total wealth after the step, 0, 0}
+ *   walk   {n, 0, 0, 0}
+ *   SIR    {S, I, R, new infections} after the step.
+ * Copies min(cap_rows, steps) rows; *rows_out = steps done.  Synchronises.
+ */
+amb_status amb_counts(amb_pop *pop, int64_t *out, size_t cap_rows, size_t *rows_out);
+
+/* Rows first .. first+n_rows-1 of the per-step counts (4 int64 each) into
+ * out (host); fails with AMB_EINVAL unless first + n_rows <= steps done.
+ * Synchronises. */
+amb_status amb_counts_range(amb_pop *pop, uint64_t first, size_t n_rows, int64_t *out);
+
+/*
+ * The counting-sort cell index of the current positions (grid environment,
+ * paper Sec. 4.1): start[C+1] with C = L*L (start[c] = agents in cells < c,
+ * start[C] = n) and ids[n] listing agent ids cell by cell (order inside a
+ * cell unspecified).  Walk and SIR.  Synchronises.
+ */
+amb_status amb_read_index(amb_pop *pop, int32_t *start, int32_t *ids, int dst_on_device);
+
+typedef struct {
+    int32_t ok;              /* 1 iff every check below holds */
+    int32_t conservation_ok; /* wealth: total wealth = n * w_init after every step */
+    int32_t nonnegative_ok;  /* wealth: no negative wealth now */
+    int32_t bounds_ok;       /* walk/SIR: every coordinate in [0, L) now */
+    int32_t population_ok;   /* SIR: S + I + R = n after every step; n fixed */
+    int32_t monotone_ok;     /* SIR: R never decreases */
+    int32_t initial_ok;      /* SIR: initial infected count = n_init_infected */
+    int32_t index_ok;        /* walk/SIR: start[C] = n, start non-decreasing */
+    int64_t first_bad_step;  /* first step whose counts failed, or -1 */
+} amb_invariant_report;
+
+/* Check the paper's invariants (Sec. 5.1.3 / 6.2) plus R monotone and index
+ * consistency.  Returns AMB_EINVARIANT when any check fails (report filled). */
+amb_status amb_invariants(amb_pop *pop, amb_invariant_report *out);
+
+typedef struct {
+    /* wealth (R17): G = sum_i (2i - n - 1) w_(i) / (n * sum w), exact integer
+     * numerator (hi, lo two's-complement 128-bit), one double division */
+    double gini;
+    int64_t gini_num_hi;
+    uint64_t gini_num_lo;
+    int64_t total_wealth;
+    int32_t min_wealth, max_wealth;
+    /* SIR curve over steps 1..T: peak I, first step at the peak, mean and
+     * variance of t weighted by I(t) from exact integer sums */
+    int64_t peak_infected;
+    uint32_t peak_step;
+    double curve_mean, curve_var;
+    int64_t final_s, final_i, final_r;
+    /* walk/SIR occupancy: the largest number of agents in one cell */
+    int32_t max_occupancy;
+} amb_stats;
+
+/* End-of-run statistics.  hist (host, optional): wealth model -> hist[v] =
+ * agents with wealth min_wealth + v; walk/SIR -> hist[m] = cells holding m
+ * agents.  Copies min(hist_cap, bins) entries, *hist_len = bins.  Synchronises. */
+amb_status amb_stats_compute(amb_pop *pop, amb_stats *out, int64_t *hist, size_t hist_cap,
+                             size_t *hist_len);
+
+/* Per-cell occupancy (C = L*L int32, host or device). Walk and SIR. */
+amb_status amb_occupancy(amb_pop *pop, int32_t *occ, int dst_on_device);
+
+/* Steps completed so far. */
+uint64_t amb_step_index(const amb_pop *pop);
+
+/* Number of CUDA kernels the step calls of this population have launched
+ * so far (amb_step only; set-up, read-back and statistics are not counted). */
+uint64_t amb_launch_count(const amb_pop *pop);
+
+/* Block until the population's queued work is done; reports device errors. */
+amb_status amb_synchronize(amb_pop *pop);
+
+/* Message of the last failure on this thread ("" if none). */
+const char *amb_last_error(void);
+
+/* SIR thresholds as the library computes them (host only, no GPU needed):
+ * t_inf[k] = min(floor((1 - (1-beta)^k) 2^32), 2^32-1), (1-beta)^k built by k
+ * IEEE double products; t_inf[0] = 0; the table ends at K (entries beyond K
+ * equal t_inf[K]), K <= cap; t_rec = min(floor(gamma 2^32), 2^32-1).
+ * t_inf needs cap+1 entries. */
+amb_status amb_sir_thresholds(double beta, double gamma, uint32_t cap, uint32_t *t_inf,
+                              uint32_t *K, uint32_t *t_rec);
+
+/*
+ * Stateless counting-sort cell index over caller buffers (grid environment,
+ * paper Sec. 4.1): x, y (n int32 each, device, values in [0, L)) -> start
+ * (C+1 int32, device, 16-byte aligned) and ids (n int32, device),
+ * C = L*L < 2^31.  Scratch
+ * (2 C int32 + look-back state) is allocated and freed on the stream.
+ * Asynchronous when sync == 0.  Agents with a coordinate outside [0, L) are
+ * left out of the index (start[C] then counts only the others, and ids
+ * beyond start[C] are unspecified); with sync != 0 the call waits for the
+ * result and returns AMB_EINVAL if any agent was left out.
+ */
+amb_status amb_cell_index(const int32_t *x, const int32_t *y, uint32_t n, uint32_t L,
+                          int32_t *start, int32_t *ids, void *cuda_stream, int sync);
+
+/* Version string of the library build. */
+const char *amb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMB_H */

@@ -1,0 +1,322 @@
+"""Python binding of the C ABI in include/amb.h (ctypes, argument marshalling
+only).  Every computation runs in libamb.so's CUDA kernels; importing this
+module fails loudly when the in-tree library is missing.
+
+Functions carry the C names.  Column buffers may be torch tensors (device or
+host) or numpy arrays (host); device tensors are passed as device pointers.
+Streams are torch.cuda.Stream objects or raw cudaStream_t integers.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libamb.so")
+
+AMB_OK, AMB_EINVAL, AMB_ENOMEM, AMB_ECUDA, AMB_EINVARIANT = 0, 1, 2, 3, 4
+AMB_ETIMEOUT, AMB_EBUSY, AMB_EBUDGET, AMB_ENOTFOUND = 5, 6, 7, 8
+STATUS_NAMES = {0: "AMB_OK", 1: "AMB_EINVAL", 2: "AMB_ENOMEM", 3: "AMB_ECUDA", 4: "AMB_EINVARIANT",
+                5: "AMB_ETIMEOUT", 6: "AMB_EBUSY", 7: "AMB_EBUDGET", 8: "AMB_ENOTFOUND"}
+
+AMB_WEALTH, AMB_WALK, AMB_SIR = 0, 1, 2
+MODELS = {"wealth": AMB_WEALTH, "walk": AMB_WALK, "sir": AMB_SIR}
+AMB_COL_WEALTH, AMB_COL_X, AMB_COL_Y, AMB_COL_STATE = 0, 1, 2, 3
+COLUMNS = {"wealth": AMB_COL_WEALTH, "x": AMB_COL_X, "y": AMB_COL_Y, "state": AMB_COL_STATE}
+AMB_S, AMB_I, AMB_R = 0, 1, 2
+AMB_SIR_AUTO, AMB_SIR_GENERIC, AMB_SIR_BAND = 0, 1, 2
+
+
+class AmbError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class amb_params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32), ("grid_side", ctypes.c_uint32), ("beta", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("n_init_infected", ctypes.c_uint32), ("w_init", ctypes.c_int32),
+                ("variant", ctypes.c_uint32)]
+
+
+class amb_invariant_report(ctypes.Structure):
+    _fields_ = [("ok", ctypes.c_int32), ("conservation_ok", ctypes.c_int32), ("nonnegative_ok", ctypes.c_int32),
+                ("bounds_ok", ctypes.c_int32), ("population_ok", ctypes.c_int32), ("monotone_ok", ctypes.c_int32),
+                ("initial_ok", ctypes.c_int32), ("index_ok", ctypes.c_int32), ("first_bad_step", ctypes.c_int64)]
+
+
+class amb_stats(ctypes.Structure):
+    _fields_ = [("gini", ctypes.c_double), ("gini_num_hi", ctypes.c_int64), ("gini_num_lo", ctypes.c_uint64),
+                ("total_wealth", ctypes.c_int64), ("min_wealth", ctypes.c_int32), ("max_wealth", ctypes.c_int32),
+                ("peak_infected", ctypes.c_int64), ("peak_step", ctypes.c_uint32), ("curve_mean", ctypes.c_double),
+                ("curve_var", ctypes.c_double), ("final_s", ctypes.c_int64), ("final_i", ctypes.c_int64),
+                ("final_r", ctypes.c_int64), ("max_occupancy", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libamb.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libamb.so not built: run __graft_entry__.build() (expected at %s)" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        vp, u32, u64, i32, sz = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_size_t
+        st = ctypes.c_int
+        sig = {
+            "amb_create": (st, [ctypes.c_int, ctypes.POINTER(amb_params), u64, u32, vp, ctypes.POINTER(vp)]),
+            "amb_destroy": (st, [vp]),
+            "amb_step": (st, [vp, u32]),
+            "amb_write_column": (st, [vp, ctypes.c_int, vp, sz, ctypes.c_int]),
+            "amb_read_column": (st, [vp, ctypes.c_int, vp, sz, ctypes.c_int]),
+            "amb_counts": (st, [vp, vp, sz, ctypes.POINTER(sz)]),
+            "amb_read_index": (st, [vp, vp, vp, ctypes.c_int]),
+            "amb_counts_range": (st, [vp, u64, sz, vp]),
+            "amb_launch_count": (u64, [vp]),
+            "amb_invariants": (st, [vp, ctypes.POINTER(amb_invariant_report)]),
+            "amb_stats_compute": (st, [vp, ctypes.POINTER(amb_stats), vp, sz, ctypes.POINTER(sz)]),
+            "amb_occupancy": (st, [vp, vp, ctypes.c_int]),
+            "amb_step_index": (u64, [vp]),
+            "amb_synchronize": (st, [vp]),
+            "amb_last_error": (ctypes.c_char_p, []),
+            "amb_sir_thresholds": (st, [ctypes.c_double, ctypes.c_double, u32, vp, ctypes.POINTER(u32),
+                                        ctypes.POINTER(u32)]),
+            "amb_cell_index": (st, [vp, vp, u32, u32, vp, vp, vp, ctypes.c_int]),
+            "amb_version": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != AMB_OK:
+        raise AmbError(rc, (lib().amb_last_error() or b"").decode(errors="replace"))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return ctypes.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _buffer(a):
+    """(pointer, on_device, element count, itemsize) of a torch tensor or numpy array."""
+    if hasattr(a, "data_ptr"):  # torch
+        if not a.is_contiguous():
+            raise ValueError("buffer must be contiguous")
+        return ctypes.c_void_p(a.data_ptr()), int(a.is_cuda), a.numel(), a.element_size()
+    a = np.asarray(a)
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("buffer must be C-contiguous")
+    return ctypes.c_void_p(a.ctypes.data), 0, a.size, a.itemsize
+
+
+# ------------------------------------------------------------------ C names --
+def amb_create(model, params, seed, replicate=0, stream=None):
+    if isinstance(model, str):
+        model = MODELS[model]
+    if isinstance(params, dict):
+        params = amb_params(**params)
+    h = ctypes.c_void_p()
+    _check(lib().amb_create(int(model), ctypes.byref(params), int(seed), int(replicate), _stream_handle(stream),
+                            ctypes.byref(h)))
+    return h
+
+
+def amb_destroy(pop):
+    _check(lib().amb_destroy(pop))
+
+
+def amb_step(pop, k=1):
+    _check(lib().amb_step(pop, int(k)))
+
+
+def amb_write_column(pop, col, src):
+    if isinstance(col, str):
+        col = COLUMNS[col]
+    p, dev, n, _ = _buffer(src)
+    _check(lib().amb_write_column(pop, int(col), p, n, dev))
+
+
+def amb_read_column(pop, col, dst):
+    if isinstance(col, str):
+        col = COLUMNS[col]
+    p, dev, n, _ = _buffer(dst)
+    _check(lib().amb_read_column(pop, int(col), p, n, dev))
+    return dst
+
+
+def amb_counts(pop, cap_rows=None):
+    steps = int(lib().amb_step_index(pop))
+    cap = steps if cap_rows is None else int(cap_rows)
+    out = np.zeros((max(cap, 1), 4), dtype=np.int64)
+    rows = ctypes.c_size_t()
+    _check(lib().amb_counts(pop, ctypes.c_void_p(out.ctypes.data), cap, ctypes.byref(rows)))
+    return out[:min(cap, rows.value)]
+
+
+def amb_counts_range(pop, first, n_rows, out=None):
+    if out is None:
+        out = np.zeros((max(int(n_rows), 1), 4), dtype=np.int64)
+    _check(lib().amb_counts_range(pop, int(first), int(n_rows), ctypes.c_void_p(out.ctypes.data)))
+    return out[:int(n_rows)]
+
+
+def amb_launch_count(pop):
+    return int(lib().amb_launch_count(pop))
+
+
+def amb_read_index(pop, start, ids):
+    ps, dev, _, _ = _buffer(start)
+    pi, dev2, _, _ = _buffer(ids)
+    if dev != dev2:
+        raise ValueError("start and ids must both be on the device or both on the host")
+    _check(lib().amb_read_index(pop, ps, pi, dev))
+    return start, ids
+
+
+def amb_invariants(pop, raise_on_violation=False):
+    r = amb_invariant_report()
+    rc = lib().amb_invariants(pop, ctypes.byref(r))
+    if rc != AMB_OK and (rc != AMB_EINVARIANT or raise_on_violation):
+        _check(rc)
+    return {f: getattr(r, f) for f, _ in amb_invariant_report._fields_}
+
+
+def amb_stats_compute(pop, hist_cap=1 << 16):
+    s = amb_stats()
+    hist = np.zeros(max(int(hist_cap), 1), dtype=np.int64)
+    ln = ctypes.c_size_t()
+    _check(lib().amb_stats_compute(pop, ctypes.byref(s), ctypes.c_void_p(hist.ctypes.data), int(hist_cap),
+                                   ctypes.byref(ln)))
+    d = {f: getattr(s, f) for f, _ in amb_stats._fields_}
+    d["gini_numerator"] = (int(d["gini_num_hi"]) << 64) | int(d["gini_num_lo"])
+    return d, hist[:min(ln.value, int(hist_cap))].copy()
+
+
+def amb_occupancy(pop, occ):
+    p, dev, _, _ = _buffer(occ)
+    _check(lib().amb_occupancy(pop, p, dev))
+    return occ
+
+
+def amb_step_index(pop):
+    return int(lib().amb_step_index(pop))
+
+
+def amb_synchronize(pop):
+    _check(lib().amb_synchronize(pop))
+
+
+def amb_last_error():
+    return (lib().amb_last_error() or b"").decode(errors="replace")
+
+
+def amb_version():
+    return lib().amb_version().decode()
+
+
+def amb_sir_thresholds(beta, gamma, cap):
+    cap = max(int(cap), 1)
+    t = np.zeros(cap + 1, dtype=np.uint32)
+    K = ctypes.c_uint32()
+    tr = ctypes.c_uint32()
+    _check(lib().amb_sir_thresholds(float(beta), float(gamma), cap, ctypes.c_void_p(t.ctypes.data),
+                                    ctypes.byref(K), ctypes.byref(tr)))
+    return t[:K.value + 1].copy(), int(tr.value)
+
+
+def amb_cell_index(x, y, L, start, ids, stream=None, sync=True):
+    px, _, n, _ = _buffer(x)
+    py, _, _, _ = _buffer(y)
+    ps, _, _, _ = _buffer(start)
+    pi, _, _, _ = _buffer(ids)
+    _check(lib().amb_cell_index(px, py, n, int(L), ps, pi, _stream_handle(stream), int(bool(sync))))
+    return start, ids
+
+
+# --------------------------------------------------------------- convenience --
+class Population:
+    """Owning wrapper around an amb_pop handle (torch tensors for columns)."""
+
+    def __init__(self, model, n, seed, rep=0, L=1, beta=0.0, gamma=0.0, n0=0, w_init=1, variant=0, stream=None):
+        self.model = model
+        self.n = int(n)
+        self.L = int(L)
+        self.params = amb_params(n=self.n, grid_side=self.L, beta=float(beta), gamma=float(gamma),
+                                 n_init_infected=int(n0), w_init=int(w_init), variant=int(variant))
+        self.handle = amb_create(model, self.params, seed, rep, stream)
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            amb_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def step(self, k=1):
+        amb_step(self.handle, k)
+        return self
+
+    @property
+    def t(self):
+        return amb_step_index(self.handle)
+
+    def column(self, name, device="cuda"):
+        import torch
+        dt = torch.uint8 if name == "state" else torch.int32
+        out = torch.empty(self.n, dtype=dt, device=device)
+        amb_read_column(self.handle, name, out)
+        return out
+
+    def write(self, name, values):
+        amb_write_column(self.handle, name, values)
+
+    def counts(self):
+        return amb_counts(self.handle)
+
+    def index(self, device="cuda"):
+        import torch
+        start = torch.empty(self.L * self.L + 1, dtype=torch.int32, device=device)
+        ids = torch.empty(max(self.n, 1), dtype=torch.int32, device=device)[: self.n]
+        amb_read_index(self.handle, start, ids)
+        return start, ids
+
+    def occupancy(self, device="cuda"):
+        import torch
+        occ = torch.empty(self.L * self.L, dtype=torch.int32, device=device)
+        amb_occupancy(self.handle, occ)
+        return occ
+
+    def invariants(self):
+        return amb_invariants(self.handle)
+
+    def stats(self, hist_cap=1 << 16):
+        return amb_stats_compute(self.handle, hist_cap)
+
+    def synchronize(self):
+        amb_synchronize(self.handle)

@@ -1,0 +1,140 @@
+// amb_internal.cuh -- population object and kernel launchers shared by the
+// library's translation units (not part of the ABI).
+#pragma once
+
+#include <vector>
+
+#include "amb_common.cuh"
+
+namespace amb {
+
+// Stream-ordered device allocation helpers; every buffer of a population is
+// allocated and freed on the population's stream.
+template <class T>
+amb_status dalloc(T **p, size_t count, cudaStream_t s)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMallocAsync((void **)p, count * sizeof(T), s);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        (void)cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? AMB_ENOMEM : AMB_ECUDA,
+                    "cudaMallocAsync(%zu bytes): %s", count * sizeof(T), cudaGetErrorString(e));
+    }
+    return AMB_OK;
+}
+
+template <class T>
+void dfree(T *&p, cudaStream_t s)
+{
+    if (p) cudaFreeAsync((void *)p, s);
+    p = nullptr;
+}
+
+// Look-back machinery shared by every single-pass scan launch of one owner:
+// tile status words (epoch tagged, never cleared) and two ticket counters
+// used alternately (each launch zeroes the counter of the next one).
+struct Lookback {
+    uint64_t *status = nullptr;
+    size_t cap = 0;
+    unsigned long long *tickets = nullptr;  // [2]
+    uint32_t launches = 0;
+
+    amb_status ensure(size_t tiles, cudaStream_t s);
+    void release(cudaStream_t s);
+    // parity and epoch of the next launch
+    void next(uint32_t *parity, uint32_t *epoch)
+    {
+        *parity = launches & 1u;
+        *epoch = (launches % 0x3FFFFFFFu) + 1u;
+        ++launches;
+    }
+};
+
+// Scan + scatter of the counting sort; scratch is owned by the caller.
+struct CellIndexScratch {
+    int32_t *cnt = nullptr;     // C
+    int32_t *cursor = nullptr;  // C
+    Lookback lb;
+};
+
+// Counting-sort cell index: start[C+1], ids[n] from id-ordered x, y.
+// `cnt` must hold C int32; `cursor` C int32.  err gets ERR_RANGE for agents
+// outside the grid (they are left out).
+amb_status launch_cell_index(const int32_t *x, const int32_t *y, uint32_t n, uint32_t L, int32_t *start,
+                             int32_t *ids, int32_t *cnt, int32_t *cursor, Lookback &lb, uint32_t *err,
+                             cudaStream_t s);
+// ids[cursor[c]++] = i for every agent i in range (cursor = copy of start).
+amb_status launch_cell_scatter(const int32_t *x, const int32_t *y, uint32_t n, uint32_t L, int32_t *cursor,
+                               int32_t *ids, cudaStream_t s);
+// Exclusive scan in[0..m) -> out[0..m], out[m] = total; out2 (optional) gets
+// the same exclusive values.
+amb_status launch_scan(const int32_t *in, int32_t *out, int32_t *out2, uint32_t m, Lookback &lb, uint32_t *err,
+                       cudaStream_t s);
+
+}  // namespace amb
+
+// Band path record layout (SIR, cell-ordered records): one uint32 "aux" per
+// record next to the agent id:
+//   [15:0]  x (L <= 65536)          [17:16] state
+//   [20:18] next move direction     [21]    next-step recovery draw passed
+//   [29:22] next-step infection code: 0 = never infected at this step;
+//           c in 1..254 = infected iff k >= c; 255 = needs k >= 255 and the
+//           exact comparison (redrawn)
+namespace amb {
+constexpr uint32_t kAuxXMask = 0xFFFFu;
+constexpr int kAuxStateShift = 16;
+constexpr int kAuxDirShift = 18;
+constexpr int kAuxRecShift = 21;
+constexpr int kAuxCodeShift = 22;
+constexpr uint32_t kCodeExact = 255u;
+constexpr uint32_t kCodeTable = 254u;  // entries 1..254 of T_inf cached in shared memory
+}  // namespace amb
+
+struct amb_pop {
+    amb_model model;
+    amb_params p;
+    uint32_t key0 = 0, key1 = 0;
+    cudaStream_t stream = nullptr;
+    uint64_t t = 0;          // steps completed
+    uint64_t launches = 0;   // kernels launched by step calls
+    uint32_t path = 0;       // SIR: AMB_SIR_GENERIC or AMB_SIR_BAND
+
+    // wealth
+    int32_t *w = nullptr;
+    int32_t *credit = nullptr;     // n, zero between steps (global path)
+    int64_t ref_total = 0;         // total wealth the conservation check expects
+    bool ref_total_valid = false;
+    uint64_t conservation_from = 0;  // first step row the conservation check covers
+    uint64_t monotone_from = 0;      // first step row the SIR count checks cover
+
+    // walk / generic SIR: id-ordered columns
+    int32_t *x = nullptr, *y = nullptr;
+    uint8_t *state = nullptr;
+    // SIR generic scratch
+    int32_t *cnt = nullptr, *inf = nullptr, *cursor = nullptr;
+    // cell index (SIR: rebuilt every step; walk: on demand)
+    int32_t *start = nullptr, *ids = nullptr;
+    bool index_valid = false;
+
+    // SIR band path: cell-ordered records, double-buffered
+    uint32_t *rec_id[2] = {nullptr, nullptr};
+    uint32_t *rec_aux[2] = {nullptr, nullptr};
+    int32_t *row_start[2] = {nullptr, nullptr};
+    int cur = 0;
+    uint32_t band_rows = 0, n_bands = 0;
+
+    // SIR thresholds
+    uint32_t *t_inf_d = nullptr;
+    std::vector<uint32_t> t_inf_h;
+    uint32_t K = 0, t_rec = 0;
+    int64_t init_infected = -1;
+
+    // per-step counts: rows of 4 int64
+    int64_t *series = nullptr;
+    size_t series_cap = 0;
+
+    amb::Lookback lb;
+    uint32_t *err = nullptr;  // device error word (sticky)
+};

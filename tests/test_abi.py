@@ -1,0 +1,65 @@
+"""CPU-only checks of the C-ABI library: it loads, exports every function that
+include/amb.h declares, and its host-side threshold tables (no GPU involved)
+equal the oracle's independently computed tables."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_16292_gb300 import amb
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+INCLUDE = os.path.join(ROOT, "include")
+
+
+def declared_functions():
+    names = set()
+    for f in os.listdir(INCLUDE):
+        if not f.endswith(".h"):
+            continue
+        text = open(os.path.join(INCLUDE, f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**\s*(amb_[a-z0-9_]+)\s*\(", text,
+                             flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_library_loads_and_exports_all_declared_symbols():
+    lib = amb.lib()
+    names = declared_functions()
+    assert len(names) >= 16
+    for name in sorted(names):
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_version_string():
+    assert "sm_103a" in amb.amb_version()
+
+
+@pytest.mark.parametrize("beta,gamma", [(0.05, 0.02), (0.01, 0.005), (0.2, 0.05), (0.123456789, 0.0333),
+                                        (0.0, 0.0), (1.0, 1.0), (1e-6, 0.5), (0.5, 1e-9)])
+def test_threshold_tables_match_oracle(beta, gamma):
+    for cap in (1, 7, 1000, 10_000_000):
+        a, ta = amb.amb_sir_thresholds(beta, gamma, cap)
+        b, tb = oracle.sir_thresholds(beta, gamma, cap)
+        assert ta == tb
+        assert np.array_equal(a, b)
+
+
+def test_threshold_rejects_bad_probabilities():
+    with pytest.raises(amb.AmbError) as e:
+        amb.amb_sir_thresholds(1.5, 0.1, 10)
+    assert e.value.status == amb.AMB_EINVAL
+    with pytest.raises(amb.AmbError):
+        amb.amb_sir_thresholds(0.1, float("nan"), 10)
+
+
+def test_params_struct_layout():
+    assert ctypes.sizeof(amb.amb_params) == 40
+    assert ctypes.sizeof(amb.amb_invariant_report) == 40
+    assert amb.amb_stats.max_occupancy.offset == 96
