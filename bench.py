@@ -264,8 +264,9 @@ def gpu_arm(args):
     amb.lib()
 
     # untimed extras first (they are short): small models and e2e
-    wealth = time_model_block(amb, torch, "wealth", WEALTH_CFG, stream, rank)
-    walk = time_model_block(amb, torch, "walk", WALK_CFG, stream, rank)
+    only_sir = args.only == "sir"
+    wealth = None if only_sir else time_model_block(amb, torch, "wealth", WEALTH_CFG, stream, rank)
+    walk = None if only_sir else time_model_block(amb, torch, "walk", WALK_CFG, stream, rank)
 
     sampler = ClockSampler(local)
     barrier(world)
@@ -277,8 +278,8 @@ def gpu_arm(args):
     clocks = sampler.stop()
     total_ms_max = max_over_ranks(world, total_ms, device)
     agent_steps = sum_over_ranks(world, float(SIR_CFG["n"]) * args.steps, device)
-    e2e = run_e2e(amb, torch, max(args.steps, 3), rank, stream)
-    e2e_val = sum_over_ranks(world, e2e["value"], device)
+    e2e = None if only_sir else run_e2e(amb, torch, max(args.steps, 3), rank, stream)
+    e2e_val = None if only_sir else sum_over_ranks(world, e2e["value"], device)
 
     if rank != 0:
         if world > 1:
@@ -319,9 +320,10 @@ def gpu_arm(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "peak_kind": peak_kind, "traffic": traffic, "bytes_per_agent_step": b_alg,
                      "kernel_ms_median": step_ms},
-        "cpu_baseline": cpu_baseline(),
-        "e2e": {"value": e2e_val, "unit": "agent-steps/s", "h2d_bytes_per_step": e2e["h2d_bytes_per_step"],
-                "d2h_bytes_per_step": e2e["d2h_bytes_per_step"]},
+        "cpu_baseline": None if only_sir else cpu_baseline(),
+        "e2e": None if only_sir else {"value": e2e_val, "unit": "agent-steps/s",
+                                      "h2d_bytes_per_step": e2e["h2d_bytes_per_step"],
+                                      "d2h_bytes_per_step": e2e["d2h_bytes_per_step"]},
         "gpu_launches": launches,
         "clocks": clocks,
         "invariants_ok": bool(inv["ok"]),
@@ -380,6 +382,8 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="amb", choices=["amb", "reference"])
+    ap.add_argument("--only", default="all", choices=["all", "sir"],
+                    help="sir: time the SIR step alone (no extras; for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -78,16 +78,19 @@ amb_status launch_scan(const int32_t *in, int32_t *out, int32_t *out2, uint32_t 
 // Band path record layout (SIR, cell-ordered records): one uint32 "aux" per
 // record next to the agent id:
 //   [15:0]  x (L <= 65536)          [17:16] state
-//   [20:18] next move direction     [21]    next-step recovery draw passed
-//   [29:22] next-step infection code: 0 = never infected at this step;
-//           c in 1..254 = infected iff k >= c; 255 = needs k >= 255 and the
-//           exact comparison (redrawn)
+//   [19:18] next move dx + 1        [21:20] next move dy + 1
+//   [22]    next-step recovery draw passed (infected agents)
+//   [30:23] next-step infection code (susceptible agents): 0 = not infected
+//           whatever k; c in 1..254 = infected iff k >= c; 255 = needs
+//           k >= 255 and the exact comparison (redrawn)
+//   [31]    always 0
 namespace amb {
 constexpr uint32_t kAuxXMask = 0xFFFFu;
 constexpr int kAuxStateShift = 16;
-constexpr int kAuxDirShift = 18;
-constexpr int kAuxRecShift = 21;
-constexpr int kAuxCodeShift = 22;
+constexpr int kAuxDxShift = 18;
+constexpr int kAuxDyShift = 20;
+constexpr int kAuxRecShift = 22;
+constexpr int kAuxCodeShift = 23;
 constexpr uint32_t kCodeExact = 255u;
 constexpr uint32_t kCodeTable = 254u;  // entries 1..254 of T_inf cached in shared memory
 }  // namespace amb
@@ -124,6 +127,8 @@ struct amb_pop {
     int32_t *row_start[2] = {nullptr, nullptr};
     int cur = 0;
     uint32_t band_rows = 0, n_bands = 0;
+    uint32_t band_grid = 0;
+    uint32_t *band_wide = nullptr;  // per-CTA 32-bit counters for bands too dense for 16-bit ones
 
     // SIR thresholds
     uint32_t *t_inf_d = nullptr;

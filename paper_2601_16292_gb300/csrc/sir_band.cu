@@ -19,18 +19,38 @@
 //   3. writes start[] for its cells and row_start for its rows;
 //   4. reads the records again and, for each agent landing in the band,
 //      applies infection (k >= the agent's precomputed code) or recovery,
-//      draws the agent's next-step Philox words (direction, infection code,
-//      recovery bit) and scatters the record to its new slot.
+//      draws the agent's next-step Philox words (move, and the infection code
+//      or recovery bit its new state needs) and scatters the record to its
+//      new slot.
 // Per-step S / I / R / new-infection counts are warp-aggregated.
+//
+// Counters.  A band whose source rows hold fewer than 65,536 records keeps
+// one 32-bit word per cell in shared memory: the low half is the agent count,
+// then (after the scan) the cell's offset inside the band, then the slot
+// cursor; the high half is the infected count.  No half can overflow because
+// every value is bounded by the band's record count.  A denser band uses two
+// 32-bit counters per cell in a per-CTA slice of global memory instead (same
+// steps, exact for any density).
+//
+// Infection code.  kmin(u1) = the smallest k in [1, K] with u1 < T_inf[k]
+// (T_inf is non-decreasing), so "u1 < T_inf[min(k, K)]" is "k >= kmin".  It is
+// found through a 256-entry table indexed by the top byte of u1 that holds
+// the range of kmin over that byte's 2^24 values, then a binary search inside
+// the range (usually empty).
 #include <algorithm>
 
 #include "amb_internal.cuh"
 
 namespace amb {
 
-constexpr int kBandNT = 1024;
-constexpr uint32_t kBandMaxCells = 24576;  // two uint32 counters per cell: 192 KiB
+constexpr int kBandNT = 512;
+constexpr int kBandCtasPerSm = 2;
+constexpr uint32_t kBandMaxCells = 24576;  // one packed uint32 per cell: 96 KiB per CTA
 constexpr int kMaxSrcRows = 256;
+constexpr uint32_t kPackedLimit = 65536;   // records per band for 16-bit halves
+constexpr int kU1 = 8;                     // independent loads per thread, pass 1
+constexpr int kU2 = 4;                     // independent loads per thread, pass 2
+constexpr uint32_t kNoCode = 255u;         // search result "no k <= 254"
 
 struct BandArgs {
     const uint32_t *id_in;
@@ -40,8 +60,10 @@ struct BandArgs {
     uint32_t *aux_out;
     int32_t *row_out;
     int32_t *start;
+    uint32_t *wide;  // 2 * H * L words per CTA, or null when n < kPackedLimit
     uint32_t n, L, H, n_bands;
     uint32_t k0, k1, t;  // t = the step executed by this launch
+    uint32_t rk0[10], rk1[10];  // Philox round keys of (k0, k1)
     const uint32_t *t_inf;
     uint32_t K, t_rec;
     int64_t *row;  // the step's count row
@@ -52,250 +74,474 @@ struct BandArgs {
     uint32_t *err;
 };
 
-// T_inf[min(k, K)] for k = 0 .. 254, and T_inf[K].
-__device__ __forceinline__ void load_tinf(uint32_t *tinf_s, const uint32_t *t_inf, uint32_t K)
+// Philox4x32-10 block for counter (c0, c1, 0, 0) with the ten round keys
+// given (they depend on the key only).
+__device__ __forceinline__ U4 philox_rk(uint32_t c0, uint32_t c1, const uint32_t *rk0, const uint32_t *rk1)
 {
-    for (uint32_t i = threadIdx.x; i <= kCodeTable; i += blockDim.x) tinf_s[i] = t_inf[i < K ? i : K];
-}
-
-// Next-step draw bits of one agent: direction (u0 >> 29), recovery bit
-// (u2 < T_rec) and the infection code of u1: the smallest k in [1, K] with
-// u1 < T_inf[k] when it is <= 254, 255 when it is larger, 0 when none.
-__device__ __forceinline__ uint32_t draw_bits(uint32_t id, uint32_t t, uint32_t k0, uint32_t k1,
-                                              const uint32_t *tinf_s, uint32_t K, uint32_t tinf_max, uint32_t t_rec)
-{
-    const U4 u = philox(id, t, k0, k1);
-    const uint32_t dir = u.w0 >> 29;
-    const uint32_t rec = (u.w2 < t_rec) ? 1u : 0u;
-    const uint32_t u1 = u.w1;
-    uint32_t k = 0;  // largest k in [0, 254] with T_inf[min(k,K)] <= u1
+    constexpr uint32_t MA = 0xD2511F53u, MB = 0xCD9E8D57u;
+    uint32_t a = c0, b = c1, c = 0u, d = 0u;
 #pragma unroll
-    for (uint32_t step = 128; step >= 1; step >>= 1)
-        if (k + step <= kCodeTable && tinf_s[k + step] <= u1) k += step;
-    uint32_t code;
-    if (k < kCodeTable)
-        code = k + 1;
-    else
-        code = (K > kCodeTable && u1 < tinf_max) ? kCodeExact : 0u;
-    return (dir << kAuxDirShift) | (rec << kAuxRecShift) | (code << kAuxCodeShift);
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t pa = (uint64_t)MA * a;
+        const uint64_t pb = (uint64_t)MB * c;
+        const uint32_t na = (uint32_t)(pb >> 32) ^ b ^ rk0[r];
+        const uint32_t nb = (uint32_t)pb;
+        const uint32_t nc = (uint32_t)(pa >> 32) ^ d ^ rk1[r];
+        const uint32_t nd = (uint32_t)pa;
+        a = na; b = nb; c = nc; d = nd;
+    }
+    return U4{a, b, c, d};
 }
 
-__device__ __forceinline__ uint32_t find_src_row(const uint32_t *srow, uint32_t nsrc, uint32_t v)
+void round_keys(uint32_t k0, uint32_t k1, uint32_t *rk0, uint32_t *rk1)
 {
-    uint32_t lo = 0, hi = nsrc - 1;
+    for (int r = 0; r < 10; ++r) {
+        rk0[r] = k0;
+        rk1[r] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+// Shared tables of the infection code: T_inf[min(k, K)] for k = 0 .. 254 and
+// the per-top-byte range of kmin, packed lo | hi << 8.
+struct CodeTables {
+    uint32_t tinf[kCodeTable + 2];
+    uint32_t range[256];
+};
+
+// first k in [lo, hi] (hi <= 255) with k == 255 or u < tinf[k]
+__device__ __forceinline__ uint32_t code_search(const uint32_t *tinf, uint32_t u, uint32_t lo, uint32_t hi)
+{
     while (lo < hi) {
-        const uint32_t mid = (lo + hi + 1) >> 1;
-        if (srow[mid] <= v)
-            lo = mid;
+        const uint32_t mid = (lo + hi) >> 1;  // mid <= 254
+        if (u < tinf[mid])
+            hi = mid;
         else
-            hi = mid - 1;
+            lo = mid + 1;
     }
     return lo;
 }
 
-__global__ void __launch_bounds__(kBandNT, 1) sir_band_kernel(const BandArgs a)
+__device__ __forceinline__ void load_code_tables(CodeTables &ct, const uint32_t *t_inf, uint32_t K)
 {
-    extern __shared__ __align__(16) uint32_t band_smem[];
-    __shared__ uint32_t tinf_s[kCodeTable + 2];
-    __shared__ uint32_t srow[kMaxSrcRows + 1];
-    __shared__ uint32_t sbase[kMaxSrcRows];
-    __shared__ uint32_t sy[kMaxSrcRows];
-    __shared__ uint32_t s_warp[kBandNT / 32 + 1];
-    __shared__ uint32_t s_band, s_prefix, s_nsrc;
-    __shared__ unsigned long long s_cnt[4];
+    for (uint32_t i = threadIdx.x; i <= kCodeTable; i += blockDim.x) ct.tinf[i] = t_inf[i < K ? i : K];
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < 256u; b += blockDim.x) {
+        const uint32_t lo = code_search(ct.tinf, b << 24, 1u, kNoCode);
+        const uint32_t hi = code_search(ct.tinf, (b << 24) | 0xFFFFFFu, 1u, kNoCode);
+        ct.range[b] = lo | (hi << 8);
+    }
+    __syncthreads();
+}
 
-    const uint32_t L = a.L, H = a.H;
-    uint32_t *cnt = band_smem;          // H*L: agents per new cell, then slot cursors
-    uint32_t *inf = band_smem + H * L;  // H*L: start-of-step infected per new cell
-    const uint32_t tid = threadIdx.x;
+// Infection code of a susceptible agent's next-step word u1.
+__device__ __forceinline__ uint32_t infection_code(const CodeTables &ct, uint32_t u1, uint32_t K, uint32_t tinf_max)
+{
+    const uint32_t r = ct.range[u1 >> 24];
+    uint32_t k = r & 0xFFu;
+    const uint32_t hi = r >> 8;
+    if (k != hi) k = code_search(ct.tinf, u1, k, hi);
+    if (k <= kCodeTable) return k;
+    return (K > kCodeTable && u1 < tinf_max) ? kCodeExact : 0u;
+}
 
-    if (blockIdx.x == 0 && tid == 0) a.tickets[a.parity ^ 1u] = 0ull;
-    load_tinf(tinf_s, a.t_inf, a.K);
-    if (tid < 4) s_cnt[tid] = 0ull;
-    const uint32_t tinf_max = a.t_inf[a.K];
-    const uint32_t t_next = a.t + 1u;
-    uint32_t cS = 0, cI = 0, cR = 0, cNew = 0;
-    const bool single = (a.n_bands == 1);
+// Next-step bits of an agent whose state (after this step) is st.
+__device__ __forceinline__ uint32_t next_bits(uint32_t id, uint32_t t, uint32_t st, const uint32_t *rk0,
+                                              const uint32_t *rk1, const CodeTables &ct, uint32_t K, uint32_t tinf_max,
+                                              uint32_t t_rec)
+{
+    const U4 u = philox_rk(id, t, rk0, rk1);
+    const uint32_t d = u.w0 >> 29;
+    uint32_t bits = (((kPackDX >> (2u * d)) & 3u) << kAuxDxShift) | (((kPackDY >> (2u * d)) & 3u) << kAuxDyShift);
+    if (st == AMB_S)
+        bits |= infection_code(ct, u.w1, K, tinf_max) << kAuxCodeShift;
+    else if (st == AMB_I)
+        bits |= (u.w2 < t_rec ? 1u : 0u) << kAuxRecShift;
+    return bits;
+}
 
-    for (;;) {
-        if (tid == 0) s_band = (uint32_t)atomicAdd(&a.tickets[a.parity], 1ull);
-        __syncthreads();
-        const uint32_t b = s_band;
-        if (b >= a.n_bands) break;
-        const uint32_t r0 = b * H;
-        const uint32_t r1 = min(r0 + H, L);
-        const uint32_t rows = r1 - r0;
-        const uint32_t cells = rows * L;
-        for (uint32_t i = tid; i < cells; i += kBandNT) {
-            cnt[i] = 0u;
-            inf[i] = 0u;
+// (x, y) + the record's move, wrapped on the torus
+__device__ __forceinline__ uint32_t wrap_step(uint32_t v, uint32_t dp /* delta + 1 */, uint32_t L)
+{
+    uint32_t s = v + dp;  // in [0, L + 1], one too large
+    s = (s == 0u) ? L : s;
+    s = (s == L + 1u) ? 1u : s;
+    return s - 1u;
+}
+
+// ------------------------------------------------------------- counters ---
+struct PackedCtr {
+    uint32_t *w;  // shared memory
+    __device__ __forceinline__ void zero(uint32_t cells) const
+    {
+        for (uint32_t i = threadIdx.x * 4u; i < cells; i += kBandNT * 4u) {
+            if (i + 3u < cells)
+                *reinterpret_cast<uint4 *>(&w[i]) = make_uint4(0u, 0u, 0u, 0u);
+            else
+                for (uint32_t e = i; e < cells; ++e) w[e] = 0u;
         }
-        if (tid == 0) {
-            const uint32_t nsrc = single ? L : rows + 2u;
-            uint32_t v = 0;
-            for (uint32_t j = 0; j < nsrc; ++j) {
-                const uint32_t y = single ? j : (r0 + L - 1u + j) % L;
-                const int32_t beg = a.row_in[y], end = a.row_in[y + 1];
-                srow[j] = v;
-                sbase[j] = (uint32_t)beg;
-                sy[j] = y;
-                v += (uint32_t)(end - beg);
-            }
-            srow[nsrc] = v;
-            s_nsrc = nsrc;
-        }
-        __syncthreads();
-        const uint32_t nsrc = s_nsrc;
-        const uint32_t M = srow[nsrc];
-
-        // pass 1: histogram of new cells and start-of-step infected per new cell
-        for (uint32_t v = tid; v < M; v += kBandNT) {
-            const uint32_t j = find_src_row(srow, nsrc, v);
-            const uint32_t s = sbase[j] + (v - srow[j]);
-            if (s >= a.n) {
-                atomicOr(a.err, ERR_RANGE);
-                continue;
-            }
-            const uint32_t aux = a.aux_in[s];
-            const uint32_t x = aux & kAuxXMask;
-            if (x >= L) {
-                atomicOr(a.err, ERR_RANGE);
-                continue;
-            }
-            const uint32_t d = (aux >> kAuxDirShift) & 7u;
-            const uint32_t yn = (uint32_t)ring_add((int32_t)sy[j], dir_dy(d), (int32_t)L);
-            if (yn < r0 || yn >= r1) continue;
-            const uint32_t xn = (uint32_t)ring_add((int32_t)x, dir_dx(d), (int32_t)L);
-            const uint32_t c = (yn - r0) * L + xn;
-            atomicAdd(&cnt[c], 1u);
-            if (((aux >> kAuxStateShift) & 3u) == AMB_I) atomicAdd(&inf[c], 1u);
-        }
-        __syncthreads();
-
-        // exclusive scan of the band's cell counts, in place
+    }
+    __device__ __forceinline__ void add(uint32_t c, bool infected) const { atomicAdd(&w[c], infected ? 0x10001u : 1u); }
+    __device__ __forceinline__ uint32_t get(uint32_t i) const { return w[i] & 0xFFFFu; }
+    __device__ __forceinline__ uint32_t infected(uint32_t c) const { return w[c] >> 16; }
+    __device__ __forceinline__ uint32_t take(uint32_t c) const { return atomicAdd(&w[c], 1u) & 0xFFFFu; }
+    // exclusive scan of the counts; the high halves are kept
+    __device__ __forceinline__ uint32_t scan(uint32_t cells, uint32_t *s_warp) const
+    {
         uint32_t running = 0;
         for (uint32_t base = 0; base < cells; base += kBandNT * 4u) {
-            const uint32_t i0 = base + tid * 4u;
+            const uint32_t i0 = base + threadIdx.x * 4u;
             uint32_t q[4];
             if (i0 + 3u < cells) {
-                const uint4 w = *reinterpret_cast<const uint4 *>(&cnt[i0]);
-                q[0] = w.x; q[1] = w.y; q[2] = w.z; q[3] = w.w;
+                const uint4 v = *reinterpret_cast<const uint4 *>(&w[i0]);
+                q[0] = v.x; q[1] = v.y; q[2] = v.z; q[3] = v.w;
             } else {
 #pragma unroll
-                for (int e = 0; e < 4; ++e) q[e] = (i0 + e < cells) ? cnt[i0 + e] : 0u;
+                for (int e = 0; e < 4; ++e) q[e] = (i0 + e < cells) ? w[i0 + e] : 0u;
             }
+            const uint32_t c0 = q[0] & 0xFFFFu, c1 = q[1] & 0xFFFFu, c2 = q[2] & 0xFFFFu, c3 = q[3] & 0xFFFFu;
             uint32_t total;
-            const uint32_t ex = block_exclusive_scan<kBandNT>(q[0] + q[1] + q[2] + q[3], s_warp, &total);
-            uint32_t e0 = running + ex;
-            uint32_t o[4];
-            o[0] = e0; o[1] = o[0] + q[0]; o[2] = o[1] + q[1]; o[3] = o[2] + q[2];
+            const uint32_t ex = block_exclusive_scan<kBandNT>(c0 + c1 + c2 + c3, s_warp, &total);
+            const uint32_t o0 = running + ex, o1 = o0 + c0, o2 = o1 + c1, o3 = o2 + c2;
+            const uint32_t r0 = (q[0] & 0xFFFF0000u) | o0, r1 = (q[1] & 0xFFFF0000u) | o1;
+            const uint32_t r2 = (q[2] & 0xFFFF0000u) | o2, r3 = (q[3] & 0xFFFF0000u) | o3;
             if (i0 + 3u < cells) {
-                *reinterpret_cast<uint4 *>(&cnt[i0]) = make_uint4(o[0], o[1], o[2], o[3]);
+                *reinterpret_cast<uint4 *>(&w[i0]) = make_uint4(r0, r1, r2, r3);
             } else {
+                const uint32_t r[4] = {r0, r1, r2, r3};
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
-                    if (i0 + e < cells) cnt[i0 + e] = o[e];
+                    if (i0 + e < cells) w[i0 + e] = r[e];
             }
             running += total;
         }
-        // first output slot of the band
-        if (tid == 0) s_prefix = lookback_exclusive(a.status, b, a.epoch, running, a.err);
-        __syncthreads();
-        const uint32_t P = s_prefix;
-        const uint32_t T = running;
+        return running;
+    }
+};
 
-        // cell index and row starts of the band
-        int32_t *start_band = a.start + (size_t)r0 * L;
-        for (uint32_t i = tid; i < cells; i += kBandNT) start_band[i] = (int32_t)(P + cnt[i]);
-        for (uint32_t r = tid; r < rows; r += kBandNT) a.row_out[r0 + r] = (int32_t)(P + cnt[r * L]);
-        if (b == a.n_bands - 1u && tid == 0) {
-            a.start[(size_t)L * L] = (int32_t)(P + T);
-            a.row_out[L] = (int32_t)(P + T);
+struct WideCtr {
+    uint32_t *cnt, *inf;  // global memory, this CTA's slice
+    __device__ __forceinline__ void zero(uint32_t cells) const
+    {
+        for (uint32_t i = threadIdx.x; i < cells; i += kBandNT) {
+            cnt[i] = 0u;
+            inf[i] = 0u;
         }
-        __syncthreads();
+        __threadfence_block();
+    }
+    __device__ __forceinline__ void add(uint32_t c, bool infected) const
+    {
+        atomicAdd(&cnt[c], 1u);
+        if (infected) atomicAdd(&inf[c], 1u);
+    }
+    __device__ __forceinline__ uint32_t get(uint32_t i) const { return cnt[i]; }
+    __device__ __forceinline__ uint32_t infected(uint32_t c) const { return inf[c]; }
+    __device__ __forceinline__ uint32_t take(uint32_t c) const { return atomicAdd(&cnt[c], 1u); }
+    __device__ __forceinline__ uint32_t scan(uint32_t cells, uint32_t *s_warp) const
+    {
+        uint32_t running = 0;
+        for (uint32_t base = 0; base < cells; base += kBandNT) {
+            const uint32_t i = base + threadIdx.x;
+            const uint32_t v = (i < cells) ? cnt[i] : 0u;
+            uint32_t total;
+            const uint32_t ex = block_exclusive_scan<kBandNT>(v, s_warp, &total);
+            if (i < cells) cnt[i] = running + ex;
+            running += total;
+        }
+        __threadfence_block();
+        return running;
+    }
+};
 
-        // pass 2: transitions, next draws, scatter
-        for (uint32_t v = tid; v < M; v += kBandNT) {
-            const uint32_t j = find_src_row(srow, nsrc, v);
-            const uint32_t s = sbase[j] + (v - srow[j]);
-            if (s >= a.n) continue;
-            const uint32_t aux = a.aux_in[s];
-            const uint32_t x = aux & kAuxXMask;
-            if (x >= L) continue;
-            const uint32_t d = (aux >> kAuxDirShift) & 7u;
-            const uint32_t yn = (uint32_t)ring_add((int32_t)sy[j], dir_dy(d), (int32_t)L);
-            if (yn < r0 || yn >= r1) continue;
-            const uint32_t xn = (uint32_t)ring_add((int32_t)x, dir_dx(d), (int32_t)L);
-            const uint32_t c = (yn - r0) * L + xn;
-            const uint32_t id = a.id_in[s];
-            uint32_t st = (aux >> kAuxStateShift) & 3u;
-            if (st == AMB_S) {
-                const uint32_t code = aux >> kAuxCodeShift;
-                const uint32_t k = inf[c];
-                if (code != 0u && k >= code) {
-                    bool hit = true;
-                    if (code == kCodeExact) {
-                        const U4 u = philox(id, a.t, a.k0, a.k1);
-                        hit = u.w1 < a.t_inf[k < a.K ? k : a.K];
-                    }
-                    if (hit) {
-                        st = AMB_I;
-                        ++cNew;
+// Warp 0: publish the band aggregate, walk back 32 predecessors at a time,
+// publish the inclusive prefix, return the exclusive prefix (all lanes).
+// Bounded like lookback_exclusive (timer + shared error word).
+__device__ __forceinline__ uint32_t warp_lookback(uint64_t *status, uint32_t tile, uint32_t epoch, uint32_t aggregate,
+                                                  uint32_t *err)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    if (tile == 0) {
+        if (lane == 0) status_store(&status[0], status_word(epoch, kFlagPrefix, aggregate));
+        return 0u;
+    }
+    if (lane == 0) status_store(&status[tile], status_word(epoch, kFlagAgg, aggregate));
+    uint32_t excl = 0;
+    int64_t base = (int64_t)tile - 1;
+    uint32_t spins = 0;
+    uint64_t t0 = 0;
+    unsigned backoff = 16;
+    while (base >= 0) {
+        const int64_t j = base - (int64_t)lane;
+        const uint64_t s = (j >= 0) ? status_load(&status[j]) : status_word(epoch, kFlagPrefix, 0u);
+        const uint64_t fl = (s >> 32) & 3ull;
+        const bool ready = ((uint32_t)(s >> 34) == epoch) && fl != 0ull;
+        const uint32_t pm = __ballot_sync(0xffffffffu, ready && fl == kFlagPrefix);
+        const uint32_t rm = __ballot_sync(0xffffffffu, ready);
+        const uint32_t last = pm ? (uint32_t)(__ffs(pm) - 1) : 31u;
+        const uint32_t need = (last == 31u) ? 0xffffffffu : ((1u << (last + 1u)) - 1u);
+        if ((rm & need) == need) {
+            uint32_t v = (lane <= last) ? (uint32_t)s : 0u;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            excl += v;
+            if (pm) break;
+            base -= 32;
+            continue;
+        }
+        if (spins == 0) t0 = global_ns();
+        bool give_up = false;
+        if ((++spins & 15u) == 0u)
+            give_up = (error_word(err) & ERR_TIMEOUT) || (global_ns() - t0 > kSpinLimitNs);
+        give_up = __shfl_sync(0xffffffffu, give_up, 0);
+        if (give_up) {
+            if (lane == 0) atomicOr(err, ERR_TIMEOUT);
+            break;
+        }
+        __nanosleep(backoff);
+        if (backoff < 256) backoff <<= 1;
+    }
+    if (lane == 0) status_store(&status[tile], status_word(epoch, kFlagPrefix, excl + aggregate));
+    return excl;
+}
+
+struct BandShared {
+    CodeTables ct;
+    uint32_t srow[kMaxSrcRows + 1];
+    uint32_t sbase[kMaxSrcRows];
+    uint32_t sy[kMaxSrcRows];
+    uint32_t warp[kBandNT / 32 + 1];
+    uint32_t band, prefix;
+    unsigned long long cnt[4];
+};
+
+struct Tally {
+    uint32_t s, i, r, fresh;
+};
+
+template <class Ctr>
+__device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, const Ctr &ctr, uint32_t b, uint32_t r0,
+                                          uint32_t r1, uint32_t M, uint32_t tinf_max, Tally &tl)
+{
+    const uint32_t L = a.L;
+    const uint32_t rows = r1 - r0;
+    const uint32_t cells = rows * L;
+    const uint32_t tid = threadIdx.x;
+    ctr.zero(cells);
+    __syncthreads();
+
+    // pass 1: agents and start-of-step infected per new cell of the band
+    {
+        uint32_t j = 0;  // source row of the thread's current record (never decreases)
+        for (uint32_t v0 = tid; v0 < M; v0 += kBandNT * kU1) {
+            uint32_t aux[kU1], yy[kU1];
+#pragma unroll
+            for (int u = 0; u < kU1; ++u) {
+                const uint32_t v = v0 + (uint32_t)u * kBandNT;
+                aux[u] = 0xFFFFFFFFu;
+                if (v < M) {
+                    while (sh.srow[j + 1] <= v) ++j;
+                    const uint32_t s = sh.sbase[j] + (v - sh.srow[j]);
+                    yy[u] = sh.sy[j];
+                    if (s < a.n) aux[u] = __ldg(&a.aux_in[s]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kU1; ++u) {
+                const uint32_t w = aux[u];
+                if (w == 0xFFFFFFFFu) continue;
+                const uint32_t x = w & kAuxXMask;
+                if (x >= L) {
+                    atomicOr(a.err, ERR_RANGE);
+                    continue;
+                }
+                const uint32_t yn = wrap_step(yy[u], (w >> kAuxDyShift) & 3u, L);
+                if (yn - r0 >= rows) continue;  // also catches yn < r0
+                const uint32_t xn = wrap_step(x, (w >> kAuxDxShift) & 3u, L);
+                ctr.add((yn - r0) * L + xn, ((w >> kAuxStateShift) & 3u) == AMB_I);
+            }
+        }
+    }
+    __syncthreads();
+
+    const uint32_t T = ctr.scan(cells, sh.warp);
+    if (tid < 32) {
+        const uint32_t P = warp_lookback(a.status, b, a.epoch, T, a.err);
+        if (tid == 0) sh.prefix = P;
+    }
+    __syncthreads();
+    const uint32_t P = sh.prefix;
+
+    // cell index and row starts of the band
+    int32_t *start_band = a.start + (size_t)r0 * L;
+    for (uint32_t i = tid; i < cells; i += kBandNT) start_band[i] = (int32_t)(P + ctr.get(i));
+    for (uint32_t r = tid; r < rows; r += kBandNT) a.row_out[r0 + r] = (int32_t)(P + ctr.get(r * L));
+    if (b == a.n_bands - 1u && tid == 0) {
+        a.start[(size_t)L * L] = (int32_t)(P + T);
+        a.row_out[L] = (int32_t)(P + T);
+    }
+    __syncthreads();
+
+    // pass 2: transitions, next draws, scatter
+    const uint32_t t_next = a.t + 1u;
+    {
+        uint32_t j = 0;
+        for (uint32_t v0 = tid; v0 < M; v0 += kBandNT * kU2) {
+            uint32_t aux[kU2], yy[kU2], ids[kU2];
+#pragma unroll
+            for (int u = 0; u < kU2; ++u) {
+                const uint32_t v = v0 + (uint32_t)u * kBandNT;
+                aux[u] = 0xFFFFFFFFu;
+                ids[u] = 0u;
+                if (v < M) {
+                    while (sh.srow[j + 1] <= v) ++j;
+                    const uint32_t s = sh.sbase[j] + (v - sh.srow[j]);
+                    yy[u] = sh.sy[j];
+                    if (s < a.n) {
+                        aux[u] = __ldg(&a.aux_in[s]);
+                        ids[u] = __ldg(&a.id_in[s]);
                     }
                 }
-            } else if (st == AMB_I) {
-                if ((aux >> kAuxRecShift) & 1u) st = AMB_R;
             }
-            cS += (st == AMB_S);
-            cI += (st == AMB_I);
-            cR += (st == AMB_R);
-            const uint32_t slot = P + atomicAdd(&cnt[c], 1u);
-            if (slot >= a.n) {
-                atomicOr(a.err, ERR_OVERFLOW);
-                continue;
+#pragma unroll
+            for (int u = 0; u < kU2; ++u) {
+                const uint32_t w = aux[u];
+                if (w == 0xFFFFFFFFu) continue;
+                const uint32_t x = w & kAuxXMask;
+                if (x >= L) continue;
+                const uint32_t yn = wrap_step(yy[u], (w >> kAuxDyShift) & 3u, L);
+                if (yn - r0 >= rows) continue;
+                const uint32_t xn = wrap_step(x, (w >> kAuxDxShift) & 3u, L);
+                const uint32_t c = (yn - r0) * L + xn;
+                const uint32_t id = ids[u];
+                uint32_t st = (w >> kAuxStateShift) & 3u;
+                if (st == AMB_S) {
+                    const uint32_t code = w >> kAuxCodeShift;
+                    if (code != 0u) {
+                        const uint32_t k = ctr.infected(c);
+                        if (k >= code) {
+                            bool hit = true;
+                            if (code == kCodeExact) {
+                                const U4 q = philox_rk(id, a.t, a.rk0, a.rk1);
+                                hit = q.w1 < a.t_inf[k < a.K ? k : a.K];
+                            }
+                            if (hit) {
+                                st = AMB_I;
+                                ++tl.fresh;
+                            }
+                        }
+                    }
+                } else if (st == AMB_I) {
+                    if ((w >> kAuxRecShift) & 1u) st = AMB_R;
+                }
+                tl.s += (st == AMB_S);
+                tl.i += (st == AMB_I);
+                tl.r += (st == AMB_R);
+                const uint32_t slot = P + ctr.take(c);
+                if (slot >= a.n) {
+                    atomicOr(a.err, ERR_OVERFLOW);
+                    continue;
+                }
+                a.id_out[slot] = id;
+                a.aux_out[slot] = xn | (st << kAuxStateShift) |
+                                  next_bits(id, t_next, st, a.rk0, a.rk1, sh.ct, a.K, tinf_max, a.t_rec);
             }
-            const uint32_t naux =
-                xn | (st << kAuxStateShift) | draw_bits(id, t_next, a.k0, a.k1, tinf_s, a.K, tinf_max, a.t_rec);
-            a.id_out[slot] = id;
-            a.aux_out[slot] = naux;
         }
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBandNT, kBandCtasPerSm) sir_band_kernel(const BandArgs a)
+{
+    extern __shared__ __align__(16) uint32_t band_smem[];
+    __shared__ BandShared sh;
+    const uint32_t L = a.L, H = a.H;
+    const uint32_t tid = threadIdx.x;
+
+    if (blockIdx.x == 0 && tid == 0) a.tickets[a.parity ^ 1u] = 0ull;
+    if (tid < 4) sh.cnt[tid] = 0ull;
+    load_code_tables(sh.ct, a.t_inf, a.K);
+    const uint32_t tinf_max = a.t_inf[a.K];
+    Tally tl = {0u, 0u, 0u, 0u};
+    const bool single = (a.n_bands == 1);
+    const PackedCtr packed{band_smem};
+    const WideCtr wide{a.wide ? a.wide + (size_t)blockIdx.x * 2u * H * L : nullptr,
+                       a.wide ? a.wide + (size_t)blockIdx.x * 2u * H * L + (size_t)H * L : nullptr};
+
+    for (;;) {
+        if (tid == 0) sh.band = (uint32_t)atomicAdd(&a.tickets[a.parity], 1ull);
         __syncthreads();
+        const uint32_t b = sh.band;
+        if (b >= a.n_bands) break;
+        const uint32_t r0 = b * H;
+        const uint32_t r1 = min(r0 + H, L);
+        // source rows r0-1 .. r1 (all rows when one band covers the grid)
+        const uint32_t nsrc = single ? L : (r1 - r0) + 2u;
+        uint32_t len = 0, beg = 0, y = 0;
+        if (tid < nsrc) {
+            y = single ? tid : (r0 + L - 1u + tid) % L;
+            const int32_t b0 = a.row_in[y], b1 = a.row_in[y + 1];
+            beg = (uint32_t)b0;
+            len = (uint32_t)(b1 - b0);
+        }
+        uint32_t M;
+        const uint32_t off = block_exclusive_scan<kBandNT>(len, sh.warp, &M);
+        if (tid < nsrc) {
+            sh.srow[tid] = off;
+            sh.sbase[tid] = beg;
+            sh.sy[tid] = y;
+        }
+        if (tid == 0) sh.srow[nsrc] = M;
+        __syncthreads();
+        if (M < kPackedLimit || a.wide == nullptr)
+            band_body(a, sh, packed, b, r0, r1, M, tinf_max, tl);
+        else
+            band_body(a, sh, wide, b, r0, r1, M, tinf_max, tl);
     }
 
     // per-step counts
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        cS += __shfl_down_sync(0xffffffffu, cS, o);
-        cI += __shfl_down_sync(0xffffffffu, cI, o);
-        cR += __shfl_down_sync(0xffffffffu, cR, o);
-        cNew += __shfl_down_sync(0xffffffffu, cNew, o);
+        tl.s += __shfl_down_sync(0xffffffffu, tl.s, o);
+        tl.i += __shfl_down_sync(0xffffffffu, tl.i, o);
+        tl.r += __shfl_down_sync(0xffffffffu, tl.r, o);
+        tl.fresh += __shfl_down_sync(0xffffffffu, tl.fresh, o);
     }
     if ((tid & 31u) == 0) {
-        if (cS) atomicAdd(&s_cnt[0], (unsigned long long)cS);
-        if (cI) atomicAdd(&s_cnt[1], (unsigned long long)cI);
-        if (cR) atomicAdd(&s_cnt[2], (unsigned long long)cR);
-        if (cNew) atomicAdd(&s_cnt[3], (unsigned long long)cNew);
+        if (tl.s) atomicAdd(&sh.cnt[0], (unsigned long long)tl.s);
+        if (tl.i) atomicAdd(&sh.cnt[1], (unsigned long long)tl.i);
+        if (tl.r) atomicAdd(&sh.cnt[2], (unsigned long long)tl.r);
+        if (tl.fresh) atomicAdd(&sh.cnt[3], (unsigned long long)tl.fresh);
     }
     __syncthreads();
-    if (tid < 4 && s_cnt[tid]) atomicAdd(reinterpret_cast<unsigned long long *>(&a.row[tid]), s_cnt[tid]);
+    if (tid < 4 && sh.cnt[tid]) atomicAdd(reinterpret_cast<unsigned long long *>(&a.row[tid]), sh.cnt[tid]);
 }
 
 // ------------------------------------------------------------- set-up ---
 // Records of the agents from id-ordered columns: ids already in cell order.
-__global__ void band_build_kernel(const uint32_t *__restrict__ ids, const int32_t *__restrict__ x,
-                                  const uint8_t *__restrict__ state, uint32_t n, uint32_t *__restrict__ aux,
-                                  uint32_t k0, uint32_t k1, uint32_t t, const uint32_t *__restrict__ t_inf,
-                                  uint32_t K, uint32_t t_rec)
+struct BuildArgs {
+    const uint32_t *ids;
+    const int32_t *x;
+    const uint8_t *state;
+    uint32_t n;
+    uint32_t *aux;
+    uint32_t t;
+    uint32_t rk0[10], rk1[10];
+    const uint32_t *t_inf;
+    uint32_t K, t_rec;
+};
+
+__global__ void band_build_kernel(const BuildArgs a)
 {
-    __shared__ uint32_t tinf_s[kCodeTable + 2];
-    load_tinf(tinf_s, t_inf, K);
-    __syncthreads();
-    const uint32_t tinf_max = t_inf[K];
-    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        const uint32_t id = ids[s];
-        if (id >= n) continue;  // only slots of agents left out of the index
-        aux[s] = (uint32_t)x[id] | ((uint32_t)state[id] << kAuxStateShift) |
-                 draw_bits(id, t, k0, k1, tinf_s, K, tinf_max, t_rec);
+    __shared__ CodeTables ct;
+    load_code_tables(ct, a.t_inf, a.K);
+    const uint32_t tinf_max = a.t_inf[a.K];
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < a.n; s += gridDim.x * blockDim.x) {
+        const uint32_t id = a.ids[s];
+        if (id >= a.n) continue;  // only slots of agents left out of the index
+        const uint32_t st = a.state[id];
+        a.aux[s] = (uint32_t)a.x[id] | (st << kAuxStateShift) |
+                   next_bits(id, a.t, st, a.rk0, a.rk1, ct, a.K, tinf_max, a.t_rec);
     }
 }
 
@@ -350,7 +596,7 @@ bool sir_band_supported(uint32_t L, uint32_t *band_rows)
     }
     const uint32_t by_smem = kBandMaxCells / L;
     const uint32_t target = std::max<uint32_t>(1u, (L + 2u * 152u - 1u) / (2u * 152u));
-    uint32_t H = std::min<uint32_t>(by_smem, std::max<uint32_t>(1u, target));
+    uint32_t H = std::min<uint32_t>(by_smem, target);
     H = std::min<uint32_t>(H, L - 2u);
     *band_rows = std::max<uint32_t>(H, 1u);
     return true;
@@ -365,12 +611,16 @@ amb_status sir_band_init(amb_pop *pop, const int32_t *x, const int32_t *y, const
     if (!sir_band_supported(L, &H)) return fail(AMB_EINVAL, "band path does not support L = %u", L);
     pop->band_rows = H;
     pop->n_bands = (L + H - 1) / H;
+    pop->band_grid = std::min<uint32_t>(pop->n_bands, (uint32_t)(sm_count() * kBandCtasPerSm));
     for (int b = 0; b < 2; ++b) {
         if (!pop->rec_id[b]) AMB_TRY(dalloc(&pop->rec_id[b], n, s));
         if (!pop->rec_aux[b]) AMB_TRY(dalloc(&pop->rec_aux[b], n, s));
         if (!pop->row_start[b]) AMB_TRY(dalloc(&pop->row_start[b], (size_t)L + 1, s));
     }
     if (!pop->start) AMB_TRY(dalloc(&pop->start, C + 1, s));
+    // 32-bit per-CTA counters for bands whose source rows hold >= 65536 agents
+    if (n >= kPackedLimit && !pop->band_wide)
+        AMB_TRY(dalloc(&pop->band_wide, (size_t)pop->band_grid * 2u * H * L, s));
     int32_t *cnt = nullptr, *cursor = nullptr;
     AMB_TRY(dalloc(&cnt, C, s));
     AMB_TRY(dalloc(&cursor, C, s));
@@ -382,9 +632,18 @@ amb_status sir_band_init(amb_pop *pop, const int32_t *x, const int32_t *y, const
     dfree(cursor, s);
     AMB_TRY(st);
     if (n) {
-        band_build_kernel<<<grid_for(n, 256, 152u * 8u), 256, 0, s>>>(pop->rec_id[nb], x, state, n, pop->rec_aux[nb],
-                                                                       pop->key0, pop->key1, (uint32_t)pop->t,
-                                                                       pop->t_inf_d, pop->K, pop->t_rec);
+        BuildArgs b;
+        b.ids = pop->rec_id[nb];
+        b.x = x;
+        b.state = state;
+        b.n = n;
+        b.aux = pop->rec_aux[nb];
+        b.t = (uint32_t)pop->t;
+        round_keys(pop->key0, pop->key1, b.rk0, b.rk1);
+        b.t_inf = pop->t_inf_d;
+        b.K = pop->K;
+        b.t_rec = pop->t_rec;
+        band_build_kernel<<<grid_for(n, 256, 152u * 8u), 256, 0, s>>>(b);
         AMB_TRY_CUDA(cudaGetLastError());
     }
     band_rows_kernel<<<grid_for((uint64_t)L + 1, 256), 256, 0, s>>>(pop->start, L, pop->row_start[nb]);
@@ -401,12 +660,12 @@ amb_status sir_band_steps(amb_pop *pop, uint32_t k)
     AMB_TRY_CUDA(cudaMemsetAsync(rows, 0, (size_t)k * 4u * sizeof(int64_t), s));
     if (pop->p.n == 0) return AMB_OK;
     const uint32_t L = pop->p.grid_side, H = pop->band_rows;
-    const size_t smem = (size_t)2u * H * L * sizeof(uint32_t);
+    const size_t smem = (size_t)H * L * sizeof(uint32_t);
     AMB_TRY_CUDA(cudaFuncSetAttribute(sir_band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const unsigned grid = std::min<unsigned>(pop->n_bands, (unsigned)sm_count());
     AMB_TRY(pop->lb.ensure(pop->n_bands, s));
+    BandArgs a;
+    round_keys(pop->key0, pop->key1, a.rk0, a.rk1);
     for (uint32_t j = 0; j < k; ++j) {
-        BandArgs a;
         const int in = pop->cur, out = pop->cur ^ 1;
         a.id_in = pop->rec_id[in];
         a.aux_in = pop->rec_aux[in];
@@ -415,6 +674,7 @@ amb_status sir_band_steps(amb_pop *pop, uint32_t k)
         a.aux_out = pop->rec_aux[out];
         a.row_out = pop->row_start[out];
         a.start = pop->start;
+        a.wide = pop->band_wide;
         a.n = pop->p.n;
         a.L = L;
         a.H = H;
@@ -430,7 +690,7 @@ amb_status sir_band_steps(amb_pop *pop, uint32_t k)
         a.status = pop->lb.status;
         pop->lb.next(&a.parity, &a.epoch);
         a.err = pop->err;
-        sir_band_kernel<<<grid, kBandNT, smem, s>>>(a);
+        sir_band_kernel<<<pop->band_grid, kBandNT, smem, s>>>(a);
         AMB_TRY_CUDA(cudaGetLastError());
         pop->cur = out;
         pop->launches += 1;
@@ -463,6 +723,7 @@ void sir_band_release(amb_pop *pop)
         dfree(pop->rec_aux[b], pop->stream);
         dfree(pop->row_start[b], pop->stream);
     }
+    dfree(pop->band_wide, pop->stream);
 }
 
 }  // namespace amb

@@ -216,6 +216,28 @@ def test_sir_band_geometries(n, L):
     g.close()
 
 
+def test_sir_band_dense_rows_use_wide_counters():
+    """150,000 agents packed into two grid rows: the bands next to them see
+    more than 65,535 source records and take the 32-bit counters, the others
+    keep the packed 16-bit ones, in the same launch."""
+    n, L = 200_000, 200
+    rng = np.random.default_rng(21)
+    y = np.where(np.arange(n) < 150_000, rng.integers(0, 2, n), rng.integers(0, L, n)).astype(np.int32)
+    x = rng.integers(0, L, n).astype(np.int32)
+    g = amb.Population("sir", n, seed=4, L=L, beta=0.05, gamma=0.02, n0=500, variant=amb.AMB_SIR_BAND)
+    o = oracle.Population("sir", n, seed=4, L=L, beta=0.05, gamma=0.02, n0=500)
+    g.write("x", x)
+    g.write("y", y)
+    o.x[:], o.y[:] = x, y
+    for k in (1, 2, 3):
+        g.step(k)
+        o.step(k)
+        assert_columns(g, o, "sir")
+    assert np.array_equal(g.counts(), o.counts())
+    assert_index(g, o)
+    g.close()
+
+
 def test_sir_band_and_generic_agree_long_run():
     kw = dict(seed=12, rep=0, L=400, beta=0.1, gamma=0.03, n0=100)
     a = amb.Population("sir", 96_000, variant=amb.AMB_SIR_BAND, **kw)
