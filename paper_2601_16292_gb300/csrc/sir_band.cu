@@ -7,9 +7,10 @@
 // (grid environment, paper Sec. 4.1).  y is implied by the row a record sits
 // in, so a record is 8 bytes.
 //
-// One step (synchronous semantics, paper Sec. 3.4).  A CTA owns a band of H
-// grid rows.  A Moore move changes y by at most one, so every agent that lands
-// in the band sits, before the move, in rows r0-1 .. r1 (torus wrap).  The CTA
+// One step (synchronous semantics, paper Sec. 3.4).  A CTA owns a band of at
+// most 32 grid rows.  A Moore move changes y by at most one, so every agent
+// that lands in the band sits, before the move, in rows r0-1 .. r1 (torus
+// wrap).  The CTA
 //   1. reads those records and counts, in shared memory, agents and
 //      start-of-step infected agents per new cell of the band (the cell
 //      histogram and the per-cell infected counts k);
@@ -17,11 +18,14 @@
 //      band's first output slot from its predecessors by decoupled look-back
 //      (bands are handed out in order by an atomic ticket);
 //   3. writes start[] for its cells and row_start for its rows;
-//   4. reads the records again and, for each agent landing in the band,
-//      applies infection (k >= the agent's precomputed code) or recovery,
-//      draws the agent's next-step Philox words (move, and the infection code
-//      or recovery bit its new state needs) and scatters the record to its
-//      new slot.
+//   4. reads the records again (now from L2) and, for each agent landing in
+//      the band, applies infection (k >= the agent's precomputed code) or
+//      recovery, draws the agent's next-step Philox words (move, and the
+//      infection code or recovery bit its new state needs) and scatters the
+//      record to its new slot.
+// While a CTA works on band b it has the bulk-copy engine prefetch into L2 the
+// records of band b + gridDim.x, the band the next round of tickets is likely
+// to hand it (a guess: a wrong one warms L2 for another CTA).
 // Per-step S / I / R / new-infection counts are warp-aggregated.
 //
 // Counters.  A band whose source rows hold fewer than 65,536 records keeps
@@ -43,14 +47,15 @@
 
 namespace amb {
 
-constexpr int kBandNT = 512;
-constexpr int kBandCtasPerSm = 2;
-constexpr uint32_t kBandMaxCells = 24576;  // one packed uint32 per cell: 96 KiB per CTA
-constexpr int kMaxSrcRows = 256;
-constexpr uint32_t kPackedLimit = 65536;   // records per band for 16-bit halves
-constexpr int kU1 = 8;                     // independent loads per thread, pass 1
-constexpr int kU2 = 4;                     // independent loads per thread, pass 2
-constexpr uint32_t kNoCode = 255u;         // search result "no k <= 254"
+constexpr int kBandNT = 1024;
+constexpr int kBandCtasPerSm = 1;
+constexpr uint32_t kBandSmem = 224u * 1024u;  // dynamic shared memory per CTA (227 KiB minus static)
+constexpr uint32_t kMaxBandRows = 32;          // tallest band (source-row tables are static)
+constexpr int kMaxSrcRows = kMaxBandRows + 2;
+constexpr uint32_t kPackedLimit = 65536;       // records per band for 16-bit halves
+constexpr int kU1 = 8;                         // independent loads per thread, pass 1
+constexpr int kU2 = 4;                         // independent loads per thread, pass 2
+constexpr uint32_t kNoCode = 255u;             // search result "no k <= 254"
 
 struct BandArgs {
     const uint32_t *id_in;
@@ -82,12 +87,12 @@ __device__ __forceinline__ U4 philox_rk(uint32_t c0, uint32_t c1, const uint32_t
     uint32_t a = c0, b = c1, c = 0u, d = 0u;
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint64_t pa = (uint64_t)MA * a;
-        const uint64_t pb = (uint64_t)MB * c;
-        const uint32_t na = (uint32_t)(pb >> 32) ^ b ^ rk0[r];
-        const uint32_t nb = (uint32_t)pb;
-        const uint32_t nc = (uint32_t)(pa >> 32) ^ d ^ rk1[r];
-        const uint32_t nd = (uint32_t)pa;
+        // high and low halves as two 32-bit multiplies (measured faster here
+        // than one widening multiply)
+        const uint32_t na = __umulhi(MB, c) ^ b ^ rk0[r];
+        const uint32_t nb = MB * c;
+        const uint32_t nc = __umulhi(MA, a) ^ d ^ rk1[r];
+        const uint32_t nd = MA * a;
         a = na; b = nb; c = nc; d = nd;
     }
     return U4{a, b, c, d};
@@ -319,6 +324,74 @@ struct Tally {
     uint32_t s, i, r, fresh;
 };
 
+// State after this step of an agent whose record (or stage) word is w and
+// whose new cell is c of the counters (infected count in the high half).
+template <class Ctr>
+__device__ __forceinline__ uint32_t new_state(const BandArgs &a, const Ctr &ctr, uint32_t c, uint32_t w, uint32_t id,
+                                              Tally &tl)
+{
+    uint32_t st = (w >> kAuxStateShift) & 3u;
+    if (st == AMB_S) {
+        const uint32_t code = (w >> kAuxCodeShift) & 0xFFu;
+        if (code != 0u) {
+            const uint32_t k = ctr.infected(c);
+            if (k >= code) {
+                bool hit = true;
+                if (code == kCodeExact) {
+                    const U4 q = philox_rk(id, a.t, a.rk0, a.rk1);
+                    hit = q.w1 < a.t_inf[k < a.K ? k : a.K];
+                }
+                if (hit) {
+                    st = AMB_I;
+                    ++tl.fresh;
+                }
+            }
+        }
+    } else if (st == AMB_I) {
+        if ((w >> kAuxRecShift) & 1u) st = AMB_R;
+    }
+    tl.s += (st == AMB_S);
+    tl.i += (st == AMB_I);
+    tl.r += (st == AMB_R);
+    return st;
+}
+
+// Write the agent's record for the next step at `slot`.
+__device__ __forceinline__ void emit(const BandArgs &a, const BandShared &sh, uint32_t slot, uint32_t id, uint32_t xn,
+                                     uint32_t st, uint32_t tinf_max)
+{
+    a.id_out[slot] = id;
+    a.aux_out[slot] =
+        xn | (st << kAuxStateShift) | next_bits(id, a.t + 1u, st, a.rk0, a.rk1, sh.ct, a.K, tinf_max, a.t_rec);
+}
+
+// L2 prefetch of global memory by the bulk-copy engine (16-byte aligned
+// start, size a multiple of 16)
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Warp 0: prefetch into L2 the records (ids and words) of the source rows of
+// band b.  Record arrays are allocated with 4 spare entries, so widening a
+// row's range to 16-byte boundaries stays inside them.
+__device__ __forceinline__ void prefetch_band(const BandArgs &a, uint32_t b, bool single)
+{
+    const uint32_t L = a.L;
+    const uint32_t r0 = (uint32_t)(((uint64_t)b * L) / a.n_bands);
+    const uint32_t r1 = (uint32_t)(((uint64_t)(b + 1u) * L) / a.n_bands);
+    const uint32_t nsrc = single ? L : (r1 - r0) + 2u;
+    for (uint32_t j = threadIdx.x; j < nsrc; j += 32u) {
+        const uint32_t y = single ? j : (r0 + L - 1u + j) % L;
+        const uint32_t s0 = (uint32_t)a.row_in[y] & ~3u;
+        const uint32_t s1 = ((uint32_t)a.row_in[y + 1] + 3u) & ~3u;
+        if (s1 > s0) {
+            prefetch_l2(a.aux_in + s0, (s1 - s0) * 4u);
+            prefetch_l2(a.id_in + s0, (s1 - s0) * 4u);
+        }
+    }
+}
+
 template <class Ctr>
 __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, const Ctr &ctr, uint32_t b, uint32_t r0,
                                           uint32_t r1, uint32_t M, uint32_t tinf_max, Tally &tl)
@@ -339,6 +412,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
             for (int u = 0; u < kU1; ++u) {
                 const uint32_t v = v0 + (uint32_t)u * kBandNT;
                 aux[u] = 0xFFFFFFFFu;
+                yy[u] = 0u;
                 if (v < M) {
                     while (sh.srow[j + 1] <= v) ++j;
                     const uint32_t s = sh.sbase[j] + (v - sh.srow[j]);
@@ -382,8 +456,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
     }
     __syncthreads();
 
-    // pass 2: transitions, next draws, scatter
-    const uint32_t t_next = a.t + 1u;
+    // pass 2: transitions, next draws, scatter (the records come from L2)
     {
         uint32_t j = 0;
         for (uint32_t v0 = tid; v0 < M; v0 += kBandNT * kU2) {
@@ -393,6 +466,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
                 const uint32_t v = v0 + (uint32_t)u * kBandNT;
                 aux[u] = 0xFFFFFFFFu;
                 ids[u] = 0u;
+                yy[u] = 0u;
                 if (v < M) {
                     while (sh.srow[j + 1] <= v) ++j;
                     const uint32_t s = sh.sbase[j] + (v - sh.srow[j]);
@@ -413,38 +487,13 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
                 if (yn - r0 >= rows) continue;
                 const uint32_t xn = wrap_step(x, (w >> kAuxDxShift) & 3u, L);
                 const uint32_t c = (yn - r0) * L + xn;
-                const uint32_t id = ids[u];
-                uint32_t st = (w >> kAuxStateShift) & 3u;
-                if (st == AMB_S) {
-                    const uint32_t code = w >> kAuxCodeShift;
-                    if (code != 0u) {
-                        const uint32_t k = ctr.infected(c);
-                        if (k >= code) {
-                            bool hit = true;
-                            if (code == kCodeExact) {
-                                const U4 q = philox_rk(id, a.t, a.rk0, a.rk1);
-                                hit = q.w1 < a.t_inf[k < a.K ? k : a.K];
-                            }
-                            if (hit) {
-                                st = AMB_I;
-                                ++tl.fresh;
-                            }
-                        }
-                    }
-                } else if (st == AMB_I) {
-                    if ((w >> kAuxRecShift) & 1u) st = AMB_R;
-                }
-                tl.s += (st == AMB_S);
-                tl.i += (st == AMB_I);
-                tl.r += (st == AMB_R);
+                const uint32_t st = new_state(a, ctr, c, w, ids[u], tl);
                 const uint32_t slot = P + ctr.take(c);
                 if (slot >= a.n) {
                     atomicOr(a.err, ERR_OVERFLOW);
                     continue;
                 }
-                a.id_out[slot] = id;
-                a.aux_out[slot] = xn | (st << kAuxStateShift) |
-                                  next_bits(id, t_next, st, a.rk0, a.rk1, sh.ct, a.K, tinf_max, a.t_rec);
+                emit(a, sh, slot, ids[u], xn, st, tinf_max);
             }
         }
     }
@@ -467,15 +516,20 @@ __global__ void __launch_bounds__(kBandNT, kBandCtasPerSm) sir_band_kernel(const
     const PackedCtr packed{band_smem};
     const WideCtr wide{a.wide ? a.wide + (size_t)blockIdx.x * 2u * H * L : nullptr,
                        a.wide ? a.wide + (size_t)blockIdx.x * 2u * H * L + (size_t)H * L : nullptr};
-
     for (;;) {
         if (tid == 0) sh.band = (uint32_t)atomicAdd(&a.tickets[a.parity], 1ull);
         __syncthreads();
         const uint32_t b = sh.band;
         if (b >= a.n_bands) break;
-        const uint32_t r0 = b * H;
-        const uint32_t r1 = min(r0 + H, L);
-        // source rows r0-1 .. r1 (all rows when one band covers the grid)
+        // the band the next wave of tickets is likely to give this CTA: have
+        // its records pulled into L2 while this one is processed (a guess;
+        // a wrong guess only warms L2 for another CTA)
+        const uint32_t ahead = b + gridDim.x;
+        if (tid < 32 && ahead < a.n_bands) prefetch_band(a, ahead, single);
+        // bands of floor / ceil(L / n_bands) rows
+        const uint32_t r0 = (uint32_t)(((uint64_t)b * L) / a.n_bands);
+        const uint32_t r1 = (uint32_t)(((uint64_t)(b + 1u) * L) / a.n_bands);
+        // source rows r0-1 .. r1 (all rows, once, when one band covers the grid)
         const uint32_t nsrc = single ? L : (r1 - r0) + 2u;
         uint32_t len = 0, beg = 0, y = 0;
         if (tid < nsrc) {
@@ -586,19 +640,41 @@ static int sm_count()
     return sms;
 }
 
+// Band geometry for an L x L grid, grid_max CTAs:
+//  * H (rows of the tallest band, <= 32) as large as the shared-memory
+//    counters allow (one word per cell);
+//  * n_bands a multiple of the grid (every CTA gets the same number of
+//    bands; band b covers rows [b L / n_bands, (b+1) L / n_bands));
+//  * one band when the whole grid fits (L <= 32).
+struct BandGeometry {
+    uint32_t H, n_bands, smem;
+};
+
+static bool band_geometry(uint32_t L, uint32_t grid_max, BandGeometry *g)
+{
+    if (L < 1 || L > 0xFFFFu || (uint64_t)L * 4u > kBandSmem) return false;
+    const uint32_t by_smem = kBandSmem / (L * 4u);
+    uint32_t H, nb;
+    if (L <= kMaxBandRows && L <= by_smem) {
+        H = L;
+        nb = 1;
+    } else {
+        const uint32_t h = std::min<uint32_t>(std::min<uint32_t>(kMaxBandRows, by_smem), L - 2u);
+        const uint32_t waves = (L + grid_max * h - 1u) / (grid_max * h);
+        nb = std::min<uint32_t>(L, grid_max * waves);
+        H = (L + nb - 1u) / nb;
+    }
+    g->H = H;
+    g->n_bands = nb;
+    g->smem = ((H * L + 3u) & ~3u) * 4u;
+    return true;
+}
+
 bool sir_band_supported(uint32_t L, uint32_t *band_rows)
 {
-    *band_rows = 0;
-    if (L < 1 || L > 0xFFFFu || L > kBandMaxCells) return false;
-    if ((uint64_t)L * L <= kBandMaxCells) {
-        *band_rows = L;  // one band holds the whole grid
-        return true;
-    }
-    const uint32_t by_smem = kBandMaxCells / L;
-    const uint32_t target = std::max<uint32_t>(1u, (L + 2u * 152u - 1u) / (2u * 152u));
-    uint32_t H = std::min<uint32_t>(by_smem, target);
-    H = std::min<uint32_t>(H, L - 2u);
-    *band_rows = std::max<uint32_t>(H, 1u);
+    BandGeometry g;
+    if (!band_geometry(L, (uint32_t)sm_count() * kBandCtasPerSm, &g)) return false;
+    *band_rows = g.H;
     return true;
 }
 
@@ -607,14 +683,18 @@ amb_status sir_band_init(amb_pop *pop, const int32_t *x, const int32_t *y, const
     cudaStream_t s = pop->stream;
     const uint32_t n = pop->p.n, L = pop->p.grid_side;
     const uint64_t C = (uint64_t)L * L;
-    uint32_t H = 0;
-    if (!sir_band_supported(L, &H)) return fail(AMB_EINVAL, "band path does not support L = %u", L);
+    const uint32_t grid_max = (uint32_t)(sm_count() * kBandCtasPerSm);
+    BandGeometry g;
+    if (!band_geometry(L, grid_max, &g)) return fail(AMB_EINVAL, "band path does not support L = %u", L);
+    const uint32_t H = g.H;
     pop->band_rows = H;
-    pop->n_bands = (L + H - 1) / H;
-    pop->band_grid = std::min<uint32_t>(pop->n_bands, (uint32_t)(sm_count() * kBandCtasPerSm));
+    pop->n_bands = g.n_bands;
+    pop->band_grid = std::min<uint32_t>(g.n_bands, grid_max);
+    pop->band_smem = g.smem;
     for (int b = 0; b < 2; ++b) {
-        if (!pop->rec_id[b]) AMB_TRY(dalloc(&pop->rec_id[b], n, s));
-        if (!pop->rec_aux[b]) AMB_TRY(dalloc(&pop->rec_aux[b], n, s));
+        // 4 spare entries: L2 prefetches of a row widen it to 16-byte boundaries
+        if (!pop->rec_id[b]) AMB_TRY(dalloc(&pop->rec_id[b], (size_t)n + 4u, s));
+        if (!pop->rec_aux[b]) AMB_TRY(dalloc(&pop->rec_aux[b], (size_t)n + 4u, s));
         if (!pop->row_start[b]) AMB_TRY(dalloc(&pop->row_start[b], (size_t)L + 1, s));
     }
     if (!pop->start) AMB_TRY(dalloc(&pop->start, C + 1, s));
@@ -659,8 +739,7 @@ amb_status sir_band_steps(amb_pop *pop, uint32_t k)
     int64_t *rows = pop->series + (size_t)pop->t * 4u;
     AMB_TRY_CUDA(cudaMemsetAsync(rows, 0, (size_t)k * 4u * sizeof(int64_t), s));
     if (pop->p.n == 0) return AMB_OK;
-    const uint32_t L = pop->p.grid_side, H = pop->band_rows;
-    const size_t smem = (size_t)H * L * sizeof(uint32_t);
+    const size_t smem = pop->band_smem;
     AMB_TRY_CUDA(cudaFuncSetAttribute(sir_band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     AMB_TRY(pop->lb.ensure(pop->n_bands, s));
     BandArgs a;
@@ -676,8 +755,8 @@ amb_status sir_band_steps(amb_pop *pop, uint32_t k)
         a.start = pop->start;
         a.wide = pop->band_wide;
         a.n = pop->p.n;
-        a.L = L;
-        a.H = H;
+        a.L = pop->p.grid_side;
+        a.H = pop->band_rows;
         a.n_bands = pop->n_bands;
         a.k0 = pop->key0;
         a.k1 = pop->key1;

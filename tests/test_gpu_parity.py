@@ -204,7 +204,7 @@ def test_sir_written_columns(variant):
 
 
 @pytest.mark.parametrize("n,L", [(24_000, 156), (25_000, 157), (300_000, 700), (600_000, 1000), (40, 900),
-                                 (200_000, 64)])
+                                 (200_000, 64), (9_000, 32), (9_000, 33), (30_000, 1), (40_000, 2), (70_000, 2)])
 def test_sir_band_geometries(n, L):
     """Single band (L*L fits one CTA), one-row bands, several-row bands with a
     short last band, nearly empty grids and dense cells, band path forced."""
