@@ -77,8 +77,10 @@ amb_status launch_scan(const int32_t *in, int32_t *out, int32_t *out2, uint32_t 
 
 // Band path record layout (SIR, cell-ordered records): one uint32 "aux" per
 // record next to the agent id:
-//   [15:0]  x (L <= 65536)          [17:16] state
-//   [19:18] next move dx + 1        [21:20] next move dy + 1
+//   [15:0]  column after the next move (L <= 65536; the current column is
+//           the cell's, found through start[])
+//   [17:16] state                   [19:18] unused
+//   [21:20] next move dy + 1
 //   [22]    next-step recovery draw passed (infected agents)
 //   [30:23] next-step infection code (susceptible agents): 0 = not infected
 //           whatever k; c in 1..254 = infected iff k >= c; 255 = needs

@@ -151,28 +151,31 @@ __device__ __forceinline__ uint32_t infection_code(const CodeTables &ct, uint32_
     return (K > kCodeTable && u1 < tinf_max) ? kCodeExact : 0u;
 }
 
-// Next-step bits of an agent whose state (after this step) is st.
-__device__ __forceinline__ uint32_t next_bits(uint32_t id, uint32_t t, uint32_t st, const uint32_t *rk0,
-                                              const uint32_t *rk1, const CodeTables &ct, uint32_t K, uint32_t tinf_max,
-                                              uint32_t t_rec)
-{
-    const U4 u = philox_rk(id, t, rk0, rk1);
-    const uint32_t d = u.w0 >> 29;
-    uint32_t bits = (((kPackDX >> (2u * d)) & 3u) << kAuxDxShift) | (((kPackDY >> (2u * d)) & 3u) << kAuxDyShift);
-    if (st == AMB_S)
-        bits |= infection_code(ct, u.w1, K, tinf_max) << kAuxCodeShift;
-    else if (st == AMB_I)
-        bits |= (u.w2 < t_rec ? 1u : 0u) << kAuxRecShift;
-    return bits;
-}
-
-// (x, y) + the record's move, wrapped on the torus
-__device__ __forceinline__ uint32_t wrap_step(uint32_t v, uint32_t dp /* delta + 1 */, uint32_t L)
+// v + (dp - 1) wrapped on a ring of L sites (v in [0, L), dp in {0, 1, 2})
+__device__ __forceinline__ uint32_t wrap_step(uint32_t v, uint32_t dp, uint32_t L)
 {
     uint32_t s = v + dp;  // in [0, L + 1], one too large
     s = (s == 0u) ? L : s;
     s = (s == L + 1u) ? 1u : s;
     return s - 1u;
+}
+
+// Record word of an agent at column x whose state (after this step) is st,
+// with its draws for step t: the column after its move, the move's dy, and
+// the infection code (susceptible) or recovery bit (infected).
+__device__ __forceinline__ uint32_t record_word(uint32_t id, uint32_t t, uint32_t st, uint32_t x, uint32_t L,
+                                                const uint32_t *rk0, const uint32_t *rk1, const CodeTables &ct,
+                                                uint32_t K, uint32_t tinf_max, uint32_t t_rec)
+{
+    const U4 u = philox_rk(id, t, rk0, rk1);
+    const uint32_t d = u.w0 >> 29;
+    uint32_t w = wrap_step(x, (kPackDX >> (2u * d)) & 3u, L) | (st << kAuxStateShift) |
+                 (((kPackDY >> (2u * d)) & 3u) << kAuxDyShift);
+    if (st == AMB_S)
+        w |= infection_code(ct, u.w1, K, tinf_max) << kAuxCodeShift;
+    else if (st == AMB_I)
+        w |= (u.w2 < t_rec ? 1u : 0u) << kAuxRecShift;
+    return w;
 }
 
 // ------------------------------------------------------------- counters ---
@@ -315,6 +318,7 @@ struct BandShared {
     uint32_t srow[kMaxSrcRows + 1];
     uint32_t sbase[kMaxSrcRows];
     uint32_t sy[kMaxSrcRows];
+    uint32_t ytab[kMaxSrcRows];  // per source row: band row reached with dy = -1, 0, +1 (a byte each, 0xFF = outside)
     uint32_t warp[kBandNT / 32 + 1];
     uint32_t band, prefix;
     unsigned long long cnt[4];
@@ -356,13 +360,12 @@ __device__ __forceinline__ uint32_t new_state(const BandArgs &a, const Ctr &ctr,
     return st;
 }
 
-// Write the agent's record for the next step at `slot`.
+// Write the agent's record for the next step at `slot` (xn: its column now).
 __device__ __forceinline__ void emit(const BandArgs &a, const BandShared &sh, uint32_t slot, uint32_t id, uint32_t xn,
                                      uint32_t st, uint32_t tinf_max)
 {
     a.id_out[slot] = id;
-    a.aux_out[slot] =
-        xn | (st << kAuxStateShift) | next_bits(id, a.t + 1u, st, a.rk0, a.rk1, sh.ct, a.K, tinf_max, a.t_rec);
+    a.aux_out[slot] = record_word(id, a.t + 1u, st, xn, a.L, a.rk0, a.rk1, sh.ct, a.K, tinf_max, a.t_rec);
 }
 
 // L2 prefetch of global memory by the bulk-copy engine (16-byte aligned
@@ -416,7 +419,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
                 if (v < M) {
                     while (sh.srow[j + 1] <= v) ++j;
                     const uint32_t s = sh.sbase[j] + (v - sh.srow[j]);
-                    yy[u] = sh.sy[j];
+                    yy[u] = sh.ytab[j];
                     if (s < a.n) aux[u] = __ldg(&a.aux_in[s]);
                 }
             }
@@ -424,15 +427,14 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
             for (int u = 0; u < kU1; ++u) {
                 const uint32_t w = aux[u];
                 if (w == 0xFFFFFFFFu) continue;
-                const uint32_t x = w & kAuxXMask;
-                if (x >= L) {
+                const uint32_t xn = w & kAuxXMask;  // column after the move
+                if (xn >= L) {
                     atomicOr(a.err, ERR_RANGE);
                     continue;
                 }
-                const uint32_t yn = wrap_step(yy[u], (w >> kAuxDyShift) & 3u, L);
-                if (yn - r0 >= rows) continue;  // also catches yn < r0
-                const uint32_t xn = wrap_step(x, (w >> kAuxDxShift) & 3u, L);
-                ctr.add((yn - r0) * L + xn, ((w >> kAuxStateShift) & 3u) == AMB_I);
+                const uint32_t yo = (yy[u] >> (8u * ((w >> kAuxDyShift) & 3u))) & 0xFFu;
+                if (yo >= rows) continue;  // lands outside the band
+                ctr.add(yo * L + xn, ((w >> kAuxStateShift) & 3u) == AMB_I);
             }
         }
     }
@@ -470,7 +472,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
                 if (v < M) {
                     while (sh.srow[j + 1] <= v) ++j;
                     const uint32_t s = sh.sbase[j] + (v - sh.srow[j]);
-                    yy[u] = sh.sy[j];
+                    yy[u] = sh.ytab[j];
                     if (s < a.n) {
                         aux[u] = __ldg(&a.aux_in[s]);
                         ids[u] = __ldg(&a.id_in[s]);
@@ -481,12 +483,11 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
             for (int u = 0; u < kU2; ++u) {
                 const uint32_t w = aux[u];
                 if (w == 0xFFFFFFFFu) continue;
-                const uint32_t x = w & kAuxXMask;
-                if (x >= L) continue;
-                const uint32_t yn = wrap_step(yy[u], (w >> kAuxDyShift) & 3u, L);
-                if (yn - r0 >= rows) continue;
-                const uint32_t xn = wrap_step(x, (w >> kAuxDxShift) & 3u, L);
-                const uint32_t c = (yn - r0) * L + xn;
+                const uint32_t xn = w & kAuxXMask;
+                if (xn >= L) continue;
+                const uint32_t yo = (yy[u] >> (8u * ((w >> kAuxDyShift) & 3u))) & 0xFFu;
+                if (yo >= rows) continue;
+                const uint32_t c = yo * L + xn;
                 const uint32_t st = new_state(a, ctr, c, w, ids[u], tl);
                 const uint32_t slot = P + ctr.take(c);
                 if (slot >= a.n) {
@@ -544,6 +545,12 @@ __global__ void __launch_bounds__(kBandNT, kBandCtasPerSm) sir_band_kernel(const
             sh.srow[tid] = off;
             sh.sbase[tid] = beg;
             sh.sy[tid] = y;
+            uint32_t tab = 0;
+            for (uint32_t dp = 0; dp < 3u; ++dp) {
+                const uint32_t yo = wrap_step(y, dp, L) - r0;  // wraps above 0xFF when outside
+                tab |= (yo < r1 - r0 ? yo : 0xFFu) << (8u * dp);
+            }
+            sh.ytab[tid] = tab;
         }
         if (tid == 0) sh.srow[nsrc] = M;
         __syncthreads();
@@ -577,7 +584,7 @@ struct BuildArgs {
     const uint32_t *ids;
     const int32_t *x;
     const uint8_t *state;
-    uint32_t n;
+    uint32_t n, L;
     uint32_t *aux;
     uint32_t t;
     uint32_t rk0[10], rk1[10];
@@ -594,8 +601,7 @@ __global__ void band_build_kernel(const BuildArgs a)
         const uint32_t id = a.ids[s];
         if (id >= a.n) continue;  // only slots of agents left out of the index
         const uint32_t st = a.state[id];
-        a.aux[s] = (uint32_t)a.x[id] | (st << kAuxStateShift) |
-                   next_bits(id, a.t, st, a.rk0, a.rk1, ct, a.K, tinf_max, a.t_rec);
+        a.aux[s] = record_word(id, a.t, st, (uint32_t)a.x[id], a.L, a.rk0, a.rk1, ct, a.K, tinf_max, a.t_rec);
     }
 }
 
@@ -607,28 +613,40 @@ __global__ void band_rows_kernel(const int32_t *__restrict__ start, uint32_t L, 
 
 // id-ordered column from the records
 __global__ void band_read_kernel(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ aux,
-                                 const int32_t *__restrict__ row_start, uint32_t n, uint32_t L, int col,
-                                 void *__restrict__ out)
+                                 const int32_t *__restrict__ row_start, const int32_t *__restrict__ start,
+                                 uint32_t n, uint32_t L, int col, void *__restrict__ out)
 {
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
         const uint32_t id = ids[s];
         if (id >= n) continue;
-        const uint32_t a = aux[s];
-        if (col == AMB_COL_X) {
-            static_cast<int32_t *>(out)[id] = (int32_t)(a & kAuxXMask);
-        } else if (col == AMB_COL_STATE) {
-            static_cast<uint8_t *>(out)[id] = (uint8_t)((a >> kAuxStateShift) & 3u);
-        } else {
-            uint32_t lo = 0, hi = L - 1;  // largest row r with row_start[r] <= s
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi + 1) >> 1;
-                if ((uint32_t)row_start[mid] <= s)
-                    lo = mid;
-                else
-                    hi = mid - 1;
-            }
-            static_cast<int32_t *>(out)[id] = (int32_t)lo;
+        if (col == AMB_COL_STATE) {
+            static_cast<uint8_t *>(out)[id] = (uint8_t)((aux[s] >> kAuxStateShift) & 3u);
+            continue;
         }
+        uint32_t lo = 0, hi = L - 1;  // row: largest r with row_start[r] <= s
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if ((uint32_t)row_start[mid] <= s)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        if (col == AMB_COL_Y) {
+            static_cast<int32_t *>(out)[id] = (int32_t)lo;
+            continue;
+        }
+        // column: largest x with start[y L + x] <= s (the record itself holds
+        // the column after the agent's next move)
+        const int32_t *row = start + (size_t)lo * L;
+        uint32_t xl = 0, xh = L - 1;
+        while (xl < xh) {
+            const uint32_t mid = (xl + xh + 1) >> 1;
+            if ((uint32_t)row[mid] <= s)
+                xl = mid;
+            else
+                xh = mid - 1;
+        }
+        static_cast<int32_t *>(out)[id] = (int32_t)xl;
     }
 }
 
@@ -717,6 +735,7 @@ amb_status sir_band_init(amb_pop *pop, const int32_t *x, const int32_t *y, const
         b.x = x;
         b.state = state;
         b.n = n;
+        b.L = L;
         b.aux = pop->rec_aux[nb];
         b.t = (uint32_t)pop->t;
         round_keys(pop->key0, pop->key1, b.rk0, b.rk1);
@@ -782,7 +801,8 @@ amb_status sir_band_read(amb_pop *pop, amb_col col, void *dst_dev)
     const uint32_t n = pop->p.n;
     if (n == 0) return AMB_OK;
     band_read_kernel<<<grid_for(n, 256, 152u * 8u), 256, 0, pop->stream>>>(
-        pop->rec_id[pop->cur], pop->rec_aux[pop->cur], pop->row_start[pop->cur], n, pop->p.grid_side, (int)col, dst_dev);
+        pop->rec_id[pop->cur], pop->rec_aux[pop->cur], pop->row_start[pop->cur], pop->start, n, pop->p.grid_side,
+        (int)col, dst_dev);
     AMB_TRY_CUDA(cudaGetLastError());
     return AMB_OK;
 }
