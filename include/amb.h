@@ -222,6 +222,29 @@ amb_status amb_sir_thresholds(double beta, double gamma, uint32_t cap, uint32_t 
 amb_status amb_cell_index(const int32_t *x, const int32_t *y, uint32_t n, uint32_t L,
                           int32_t *start, int32_t *ids, void *cuda_stream, int sync);
 
+/*
+ * amb_cell_index without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory while they run, for example a process whose device memory is
+ * all handed out by another allocator up front (a fixed HBM budget), or code
+ * that must not call cudaMalloc / cudaFree because those can synchronise the
+ * whole device.  The caller passes inputs and outputs exactly as for
+ * amb_cell_index; the scratch (cell counts, cursors, look-back words, error
+ * word) is a file-scope device array of about 8 MiB, for grids of at most
+ * 1,048,576 cells (L <= 1024); larger grids return AMB_EINVAL.  Every GPU that
+ * loads the library keeps that array until the process exits.
+ *  - The first call on a device, with that device current, looks up the
+ *    array's device address (cudaGetSymbolAddress); make that first call
+ *    before any stream capture.
+ *  - All calls share the one array and it keeps the last call's contents;
+ *    the call clears what has to start at zero.  Calls that overlap on the
+ *    GPU (other streams, other threads) race on it: serialise them.
+ *  - sync != 0 waits for the result and reports coordinates outside [0, L)
+ *    as AMB_EINVAL, as amb_cell_index does.
+ */
+amb_status amb_cell_index_noalloc(const int32_t *x, const int32_t *y, uint32_t n, uint32_t L, int32_t *start,
+                                  int32_t *ids, void *cuda_stream, int sync);
+
 /* Version string of the library build. */
 const char *amb_version(void);
 

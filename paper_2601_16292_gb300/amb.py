@@ -84,6 +84,7 @@ def lib():
             "amb_sir_thresholds": (st, [ctypes.c_double, ctypes.c_double, u32, vp, ctypes.POINTER(u32),
                                         ctypes.POINTER(u32)]),
             "amb_cell_index": (st, [vp, vp, u32, u32, vp, vp, vp, ctypes.c_int]),
+            "amb_cell_index_noalloc": (st, [vp, vp, u32, u32, vp, vp, vp, ctypes.c_int]),
             "amb_version": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -246,6 +247,17 @@ def amb_cell_index(x, y, L, start, ids, stream=None, sync=True):
     ps, _, _, _ = _buffer(start)
     pi, _, _, _ = _buffer(ids)
     _check(lib().amb_cell_index(px, py, n, int(L), ps, pi, _stream_handle(stream), int(bool(sync))))
+    return start, ids
+
+
+def amb_cell_index_noalloc(x, y, L, start, ids, stream=None, sync=True):
+    """amb_cell_index with its scratch in the library's static device array
+    (no allocation; grids of at most 1,048,576 cells)."""
+    px, _, n, _ = _buffer(x)
+    py, _, _, _ = _buffer(y)
+    ps, _, _, _ = _buffer(start)
+    pi, _, _, _ = _buffer(ids)
+    _check(lib().amb_cell_index_noalloc(px, py, n, int(L), ps, pi, _stream_handle(stream), int(bool(sync))))
     return start, ids
 
 

@@ -65,6 +65,15 @@ struct CellIndexScratch {
 amb_status launch_cell_index(const int32_t *x, const int32_t *y, uint32_t n, uint32_t L, int32_t *start,
                              int32_t *ids, int32_t *cnt, int32_t *cursor, Lookback &lb, uint32_t *err,
                              cudaStream_t s);
+// The same index with every scratch buffer supplied by the caller (allocates
+// nothing): cnt and cursor hold C int32, status scan_tiles(C) words, tickets
+// two counters whose `parity` one is zero; epoch and parity advance per call
+// as Lookback::next does.
+uint32_t scan_tiles(uint32_t m);
+amb_status launch_cell_index_raw(const int32_t *x, const int32_t *y, uint32_t n, uint32_t L, int32_t *start,
+                                 int32_t *ids, int32_t *cnt, int32_t *cursor, uint64_t *status,
+                                 unsigned long long *tickets, uint32_t parity, uint32_t epoch, uint32_t *err,
+                                 cudaStream_t s);
 // ids[cursor[c]++] = i for every agent i in range (cursor = copy of start).
 amb_status launch_cell_scatter(const int32_t *x, const int32_t *y, uint32_t n, uint32_t L, int32_t *cursor,
                                int32_t *ids, cudaStream_t s);

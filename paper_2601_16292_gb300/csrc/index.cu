@@ -118,6 +118,8 @@ amb_status launch_scan(const int32_t *in, int32_t *out, int32_t *out2, uint32_t 
     return AMB_OK;
 }
 
+uint32_t scan_tiles(uint32_t m) { return (uint32_t)(((uint64_t)m + kScanTile - 1) / kScanTile); }
+
 // ------------------------------------------------------ histogram/scatter ---
 __global__ void cell_hist_kernel(const int32_t *__restrict__ x, const int32_t *__restrict__ y, uint32_t n,
                                  int32_t L, int32_t *__restrict__ cnt, uint32_t *err)
@@ -149,6 +151,31 @@ amb_status launch_cell_scatter(const int32_t *x, const int32_t *y, uint32_t n, u
     if (n == 0) return AMB_OK;
     cell_scatter_kernel<<<grid_for(n, 256), 256, 0, s>>>(x, y, n, (int32_t)L, cursor, ids);
     AMB_TRY_CUDA(cudaGetLastError());
+    return AMB_OK;
+}
+
+amb_status launch_cell_index_raw(const int32_t *x, const int32_t *y, uint32_t n, uint32_t L, int32_t *start,
+                                 int32_t *ids, int32_t *cnt, int32_t *cursor, uint64_t *status,
+                                 unsigned long long *tickets, uint32_t parity, uint32_t epoch, uint32_t *err,
+                                 cudaStream_t s)
+{
+    const uint64_t C = (uint64_t)L * L;
+    const uint32_t n_tiles = scan_tiles((uint32_t)C);
+    AMB_TRY_CUDA(cudaMemsetAsync(cnt, 0, C * sizeof(int32_t), s));
+    if (n) {
+        cell_hist_kernel<<<grid_for(n, 256), 256, 0, s>>>(x, y, n, (int32_t)L, cnt, err);
+        AMB_TRY_CUDA(cudaGetLastError());
+    }
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned grid = (unsigned)std::min<uint64_t>(n_tiles, (uint64_t)sms * 8u);
+    scan_kernel<<<grid, kScanNT, 0, s>>>(cnt, start, cursor, (uint32_t)C, n_tiles, tickets, parity, status, epoch, err);
+    AMB_TRY_CUDA(cudaGetLastError());
+    if (n) {
+        cell_scatter_kernel<<<grid_for(n, 256), 256, 0, s>>>(x, y, n, (int32_t)L, cursor, ids);
+        AMB_TRY_CUDA(cudaGetLastError());
+    }
     return AMB_OK;
 }
 
