@@ -222,6 +222,57 @@ amb_status amb_sir_thresholds(double beta, double gamma, uint32_t cap, uint32_t 
 amb_status amb_cell_index(const int32_t *x, const int32_t *y, uint32_t n, uint32_t L,
                           int32_t *start, int32_t *ids, void *cuda_stream, int sync);
 
+/* ------------------------------------------------------------ batches ----
+ * Many independent jobs advanced together on one GPU (the paper's Experiment
+ * with replications and ParallelRunner, Sec. 4.2, re-cast for one device):
+ * every SIR step of every job is one shared launch over all their bands; small
+ * wealth jobs run in one launch, one CTA each; large wealth jobs take three
+ * shared launches per step; walk jobs one launch each.  The run is captured
+ * into one CUDA graph and launched once (use_graph = 1, the default).
+ * Results are bit-identical to stepping each job alone with amb_step.
+ */
+typedef struct {
+    amb_model model;
+    amb_params params;   /* SIR jobs run on the band path (variant GENERIC is rejected) */
+    uint64_t seed;
+    uint32_t replicate;
+    uint32_t steps;      /* steps this job advances in amb_batch_run */
+} amb_job;
+
+typedef struct {
+    uint32_t band_rows_cap; /* tallest SIR band in rows (1..32); 0 = 32 */
+    int32_t autotune;       /* 1: time caps 8, 16, 32 on throwaway copies of up to eight
+                               of the largest SIR jobs and keep the fastest */
+    int32_t use_graph;      /* 1: one CUDA graph for the whole run */
+} amb_tune;
+
+typedef struct {
+    size_t n_jobs;
+    uint32_t band_rows_cap; /* the cap used */
+    uint64_t launches;      /* kernel launches of the run */
+    uint64_t agent_steps;   /* sum over jobs of n * steps */
+    double ms;              /* device time of the run (events around the graph launch) */
+} amb_batch_report;
+
+typedef struct amb_batch amb_batch;
+
+/* Create the populations of n jobs (device memory on cuda_stream, which must
+ * not be the legacy default stream when graphs are used). */
+amb_status amb_batch_create(const amb_job *jobs, size_t n, void *cuda_stream, amb_batch **out);
+
+/* Advance every job by its steps (once per batch); tune may be NULL (cap 32,
+ * no autotune, graph).  *ms_out (optional): device time of the run. */
+amb_status amb_batch_run(amb_batch *b, const amb_tune *tune, double *ms_out);
+
+/* Borrow job i's population (read columns, counts, statistics through the
+ * single-population calls; the batch keeps ownership). */
+amb_status amb_batch_population(amb_batch *b, size_t i, amb_pop **pop);
+
+amb_status amb_batch_info(amb_batch *b, amb_batch_report *info);
+
+/* Free every population of the batch. */
+amb_status amb_batch_destroy(amb_batch *b);
+
 /*
  * amb_cell_index without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate

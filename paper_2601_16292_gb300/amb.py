@@ -53,6 +53,20 @@ class amb_stats(ctypes.Structure):
                 ("final_r", ctypes.c_int64), ("max_occupancy", ctypes.c_int32)]
 
 
+class amb_job(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int), ("params", amb_params), ("seed", ctypes.c_uint64),
+                ("replicate", ctypes.c_uint32), ("steps", ctypes.c_uint32)]
+
+
+class amb_tune(ctypes.Structure):
+    _fields_ = [("band_rows_cap", ctypes.c_uint32), ("autotune", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+
+
+class amb_batch_report(ctypes.Structure):
+    _fields_ = [("n_jobs", ctypes.c_size_t), ("band_rows_cap", ctypes.c_uint32), ("launches", ctypes.c_uint64),
+                ("agent_steps", ctypes.c_uint64), ("ms", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -86,6 +100,11 @@ def lib():
             "amb_cell_index": (st, [vp, vp, u32, u32, vp, vp, vp, ctypes.c_int]),
             "amb_cell_index_noalloc": (st, [vp, vp, u32, u32, vp, vp, vp, ctypes.c_int]),
             "amb_version": (ctypes.c_char_p, []),
+            "amb_batch_create": (st, [vp, sz, vp, ctypes.POINTER(vp)]),
+            "amb_batch_run": (st, [vp, ctypes.POINTER(amb_tune), ctypes.POINTER(ctypes.c_double)]),
+            "amb_batch_population": (st, [vp, sz, ctypes.POINTER(vp)]),
+            "amb_batch_info": (st, [vp, ctypes.POINTER(amb_batch_report)]),
+            "amb_batch_destroy": (st, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -261,6 +280,47 @@ def amb_cell_index_noalloc(x, y, L, start, ids, stream=None, sync=True):
     return start, ids
 
 
+def make_job(model, n, seed, steps, rep=0, L=1, beta=0.0, gamma=0.0, n0=0, w_init=1):
+    """amb_job from keyword arguments (the same names as Population)."""
+    if isinstance(model, str):
+        model = MODELS[model]
+    return amb_job(model=int(model), params=amb_params(n=int(n), grid_side=int(L), beta=float(beta),
+                                                       gamma=float(gamma), n_init_infected=int(n0),
+                                                       w_init=int(w_init), variant=0),
+                   seed=int(seed), replicate=int(rep), steps=int(steps))
+
+
+def amb_batch_create(jobs, stream=None):
+    arr = (amb_job * max(len(jobs), 1))(*jobs)
+    h = ctypes.c_void_p()
+    _check(lib().amb_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(jobs), _stream_handle(stream),
+                                  ctypes.byref(h)))
+    return h
+
+
+def amb_batch_run(batch, band_rows_cap=0, autotune=False, use_graph=True):
+    t = amb_tune(band_rows_cap=int(band_rows_cap), autotune=int(bool(autotune)), use_graph=int(bool(use_graph)))
+    ms = ctypes.c_double()
+    _check(lib().amb_batch_run(batch, ctypes.byref(t), ctypes.byref(ms)))
+    return ms.value
+
+
+def amb_batch_population(batch, i):
+    h = ctypes.c_void_p()
+    _check(lib().amb_batch_population(batch, int(i), ctypes.byref(h)))
+    return h
+
+
+def amb_batch_info(batch):
+    r = amb_batch_report()
+    _check(lib().amb_batch_info(batch, ctypes.byref(r)))
+    return {f: getattr(r, f) for f, _ in amb_batch_report._fields_}
+
+
+def amb_batch_destroy(batch):
+    _check(lib().amb_batch_destroy(batch))
+
+
 # --------------------------------------------------------------- convenience --
 class Population:
     """Owning wrapper around an amb_pop handle (torch tensors for columns)."""
@@ -332,3 +392,45 @@ class Population:
 
     def synchronize(self):
         amb_synchronize(self.handle)
+
+
+class PopulationView(Population):
+    """Non-owning view of a population that belongs to a batch or server."""
+
+    def __init__(self, handle, model, n, L=1):
+        self.model = model
+        self.n = int(n)
+        self.L = int(L)
+        self.handle = handle
+
+    def close(self):
+        self.handle = None
+
+
+class Batch:
+    """Owning wrapper around amb_batch: jobs are dicts of make_job keywords."""
+
+    def __init__(self, jobs, stream=None):
+        self.specs = [dict(j) for j in jobs]
+        self.handle = amb_batch_create([make_job(**j) for j in self.specs], stream)
+
+    def run(self, band_rows_cap=0, autotune=False, use_graph=True):
+        return amb_batch_run(self.handle, band_rows_cap, autotune, use_graph)
+
+    def info(self):
+        return amb_batch_info(self.handle)
+
+    def population(self, i):
+        s = self.specs[i]
+        return PopulationView(amb_batch_population(self.handle, i), s["model"], s["n"], s.get("L", 1))
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            amb_batch_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -77,6 +77,42 @@ amb_status launch_cell_index_raw(const int32_t *x, const int32_t *y, uint32_t n,
 // ids[cursor[c]++] = i for every agent i in range (cursor = copy of start).
 amb_status launch_cell_scatter(const int32_t *x, const int32_t *y, uint32_t n, uint32_t L, int32_t *cursor,
                                int32_t *ids, cudaStream_t s);
+// ---- batches: many populations advanced by shared launches ----
+// Wealth populations: the small ones (column fits one CTA's shared memory)
+// run all their steps in one launch, one CTA per population; the large ones
+// take three launches per step over the concatenation of their columns.
+struct WealthBatch {
+    void *d_jobs = nullptr;
+    uint32_t *d_small = nullptr, *d_large = nullptr, *d_prefix = nullptr;
+    uint32_t n_jobs = 0, n_small = 0, n_large = 0, large_chunks = 0;
+    size_t smem = 0;
+};
+bool wealth_uses_smem(uint32_t n);
+amb_status wealth_batch_build(WealthBatch &wb, amb_pop **pops, const uint32_t *steps, uint32_t n, cudaStream_t s);
+amb_status wealth_batch_small(WealthBatch &wb, cudaStream_t s, uint64_t *launches);
+amb_status wealth_batch_large_step(WealthBatch &wb, cudaStream_t s, uint64_t *launches);
+void wealth_batch_release(WealthBatch &wb, cudaStream_t s);
+
+// SIR populations on the band path: one launch per step covers the bands of
+// every population (plus one small launch that advances their steps).
+struct SirBatch {
+    void *d_jobs = nullptr;
+    uint32_t *d_prefix = nullptr, *d_codes = nullptr, *wide = nullptr;
+    unsigned long long *tickets = nullptr;
+    uint32_t n_jobs = 0, total_bands = 0, grid = 0, wide_words = 0;
+    uint32_t epoch_base = 0, launches = 0;
+    size_t smem = 0;
+};
+amb_status sir_batch_build(SirBatch &sb, amb_pop **pops, const uint32_t *steps, uint32_t n, uint32_t rows_cap,
+                           cudaStream_t s);
+amb_status sir_batch_step(SirBatch &sb, cudaStream_t s, uint64_t *launches);
+// hand the populations back to single stepping after `steps[q]` batched steps
+void sir_batch_finish(SirBatch &sb, amb_pop **pops, const uint32_t *steps, uint32_t n);
+void sir_batch_release(SirBatch &sb, cudaStream_t s);
+
+// Step-count rows of a population: capacity for `rows` steps.
+amb_status ensure_series(amb_pop *pop, uint64_t rows);
+
 // Exclusive scan in[0..m) -> out[0..m], out[m] = total; out2 (optional) gets
 // the same exclusive values.
 amb_status launch_scan(const int32_t *in, int32_t *out, int32_t *out2, uint32_t m, Lookback &lb, uint32_t *err,

@@ -143,7 +143,7 @@ static amb_status device_error(amb_pop *pop)
     return AMB_OK;
 }
 
-static amb_status ensure_series(amb_pop *pop, uint64_t rows)
+amb_status ensure_series(amb_pop *pop, uint64_t rows)
 {
     if (rows <= pop->series_cap) return AMB_OK;
     size_t cap = pop->series_cap ? pop->series_cap : 64;

@@ -8,6 +8,8 @@
 //    two grid-wide kernels per step;
 //  * SIR, generic path: move + cell histogram, counting-sort index, and the
 //    infection / recovery pass reading the per-cell infected counts.
+#include <algorithm>
+
 #include "amb_internal.cuh"
 
 namespace amb {
@@ -67,9 +69,8 @@ __device__ __forceinline__ uint32_t lanemask_lt()
 }
 
 // One CTA, whole column resident in shared memory, k steps.
-__global__ void __launch_bounds__(kWealthNT) wealth_smem_kernel(int32_t *__restrict__ wg, uint32_t n, uint32_t k0,
-                                                                uint32_t k1, uint32_t t0, uint32_t k,
-                                                                int64_t *__restrict__ series)
+__device__ __forceinline__ void wealth_cta_steps(int32_t *__restrict__ wg, uint32_t n, uint32_t k0, uint32_t k1,
+                                                 uint32_t t0, uint32_t k, int64_t *__restrict__ series)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int32_t *w = reinterpret_cast<int32_t *>(smem_raw);
@@ -134,6 +135,189 @@ __global__ void __launch_bounds__(kWealthNT) wealth_smem_kernel(int32_t *__restr
         __syncthreads();
     }
     for (uint32_t i = threadIdx.x; i < n; i += kWealthNT) wg[i] = w[i];
+}
+
+__global__ void __launch_bounds__(kWealthNT) wealth_smem_kernel(int32_t *__restrict__ wg, uint32_t n, uint32_t k0,
+                                                                uint32_t k1, uint32_t t0, uint32_t k,
+                                                                int64_t *__restrict__ series)
+{
+    wealth_cta_steps(wg, n, k0, k1, t0, k, series);
+}
+
+// ------------------------------------------------------- wealth batches ---
+// Device descriptor of one wealth population in a batch.
+struct WealthJob {
+    int32_t *w;
+    int32_t *credit;  // large populations
+    int64_t *series;  // row 0 = the population's step 0
+    uint32_t n, k0, k1, t, t_end, pad;
+};
+
+// Small populations: one CTA per job runs all its remaining steps.
+__global__ void __launch_bounds__(kWealthNT) wealth_batch_small_kernel(WealthJob *__restrict__ jobs,
+                                                                       const uint32_t *__restrict__ list)
+{
+    WealthJob &j = jobs[list[blockIdx.x]];
+    if (j.t < j.t_end) wealth_cta_steps(j.w, j.n, j.k0, j.k1, j.t, j.t_end - j.t, j.series + (size_t)j.t * 4u);
+}
+
+constexpr uint32_t kWealthChunk = 2048;  // agents per block in the batched grid-wide kernels
+
+__device__ __forceinline__ uint32_t chunk_job(const uint32_t *prefix, uint32_t n_jobs, uint32_t g)
+{
+    uint32_t lo = 0, hi = n_jobs - 1;  // last job whose first chunk <= g
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= g)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Large populations, one step: donors credit their recipients (phase 1).
+__global__ void __launch_bounds__(256) wealth_batch_donate_kernel(const WealthJob *__restrict__ jobs,
+                                                                  const uint32_t *__restrict__ list,
+                                                                  const uint32_t *__restrict__ prefix, uint32_t n_jobs)
+{
+    __shared__ uint32_t s_job;
+    if (threadIdx.x == 0) s_job = chunk_job(prefix, n_jobs, blockIdx.x);
+    __syncthreads();
+    const WealthJob &j = jobs[list[s_job]];
+    if (j.t >= j.t_end) return;
+    const uint32_t first = (blockIdx.x - prefix[s_job]) * kWealthChunk;
+    const uint32_t last = min(first + kWealthChunk, j.n);
+    uint32_t local = 0;
+    for (uint32_t i = first + threadIdx.x; i < last; i += blockDim.x) {
+        if (j.w[i] > 0) {
+            const U4 u = philox(i, j.t, j.k0, j.k1);
+            uint32_t r = below(u.w0, j.n - 1u);
+            r += (r >= i) ? 1u : 0u;
+            atomicAdd(&j.credit[r], 1);
+            ++local;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_down_sync(0xffffffffu, local, o);
+    if ((threadIdx.x & 31) == 0 && local)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&j.series[(size_t)j.t * 4u]), (unsigned long long)local);
+}
+
+// Large populations, one step: w' = w - [w > 0] + credit (phase 2).
+__global__ void __launch_bounds__(256) wealth_batch_apply_kernel(const WealthJob *__restrict__ jobs,
+                                                                 const uint32_t *__restrict__ list,
+                                                                 const uint32_t *__restrict__ prefix, uint32_t n_jobs)
+{
+    __shared__ uint32_t s_job;
+    if (threadIdx.x == 0) s_job = chunk_job(prefix, n_jobs, blockIdx.x);
+    __syncthreads();
+    const WealthJob &j = jobs[list[s_job]];
+    if (j.t >= j.t_end) return;
+    const uint32_t first = (blockIdx.x - prefix[s_job]) * kWealthChunk;
+    const uint32_t last = min(first + kWealthChunk, j.n);
+    long long part = 0;
+    for (uint32_t i = first + threadIdx.x; i < last; i += blockDim.x) {
+        const int32_t wi = j.w[i];
+        const int32_t nw = (int32_t)((uint32_t)wi - (wi > 0 ? 1u : 0u) + (uint32_t)j.credit[i]);
+        j.w[i] = nw;
+        j.credit[i] = 0;
+        part += nw;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0 && part)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&j.series[(size_t)j.t * 4u + 1u]), (unsigned long long)part);
+}
+
+__global__ void wealth_batch_advance_kernel(WealthJob *__restrict__ jobs, const uint32_t *__restrict__ list,
+                                            uint32_t n_jobs)
+{
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n_jobs; q += gridDim.x * blockDim.x) {
+        WealthJob &j = jobs[list[q]];
+        if (j.t < j.t_end) j.t += 1u;
+    }
+}
+
+// Host side: a set of wealth populations advanced together.
+amb_status wealth_batch_build(WealthBatch &wb, amb_pop **pops, const uint32_t *steps, uint32_t n, cudaStream_t s)
+{
+    std::vector<WealthJob> jobs(n);
+    std::vector<uint32_t> small, large, prefix(1, 0u);
+    size_t smem = 16;
+    for (uint32_t q = 0; q < n; ++q) {
+        amb_pop *p = pops[q];
+        WealthJob &j = jobs[q];
+        j.w = p->w;
+        j.credit = p->credit;
+        j.series = p->series;
+        j.n = p->p.n;
+        j.k0 = p->key0;
+        j.k1 = p->key1;
+        j.t = (uint32_t)p->t;
+        j.t_end = (uint32_t)(p->t + steps[q]);
+        j.pad = 0;
+        if (p->p.n == 0 || steps[q] == 0) continue;
+        if (wealth_uses_smem(p->p.n)) {
+            small.push_back(q);
+            smem = std::max(smem, (size_t)((p->p.n + 7u) & ~7u) * 4u + (size_t)p->p.n * 2u + 16u);
+        } else {
+            large.push_back(q);
+            prefix.push_back(prefix.back() + (p->p.n + kWealthChunk - 1u) / kWealthChunk);
+        }
+    }
+    wb.n_jobs = n;
+    wb.n_small = (uint32_t)small.size();
+    wb.n_large = (uint32_t)large.size();
+    wb.large_chunks = prefix.back();
+    wb.smem = smem;
+    AMB_TRY(dalloc(reinterpret_cast<unsigned char **>(&wb.d_jobs), (size_t)n * sizeof(WealthJob), s));
+    AMB_TRY(dalloc(&wb.d_small, small.size(), s));
+    AMB_TRY(dalloc(&wb.d_large, large.size(), s));
+    AMB_TRY(dalloc(&wb.d_prefix, prefix.size(), s));
+    AMB_TRY_CUDA(cudaMemcpyAsync(wb.d_jobs, jobs.data(), (size_t)n * sizeof(WealthJob), cudaMemcpyHostToDevice, s));
+    if (!small.empty())
+        AMB_TRY_CUDA(cudaMemcpyAsync(wb.d_small, small.data(), small.size() * 4u, cudaMemcpyHostToDevice, s));
+    if (!large.empty())
+        AMB_TRY_CUDA(cudaMemcpyAsync(wb.d_large, large.data(), large.size() * 4u, cudaMemcpyHostToDevice, s));
+    AMB_TRY_CUDA(cudaMemcpyAsync(wb.d_prefix, prefix.data(), prefix.size() * 4u, cudaMemcpyHostToDevice, s));
+    AMB_TRY_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
+    return AMB_OK;
+}
+
+// Every small job, all of its steps (one launch).
+amb_status wealth_batch_small(WealthBatch &wb, cudaStream_t s, uint64_t *launches)
+{
+    if (wb.n_small == 0) return AMB_OK;
+    AMB_TRY_CUDA(cudaFuncSetAttribute(wealth_batch_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)wb.smem));
+    wealth_batch_small_kernel<<<wb.n_small, kWealthNT, wb.smem, s>>>(static_cast<WealthJob *>(wb.d_jobs), wb.d_small);
+    AMB_TRY_CUDA(cudaGetLastError());
+    *launches += 1;
+    return AMB_OK;
+}
+
+// One step of every large job (three launches).
+amb_status wealth_batch_large_step(WealthBatch &wb, cudaStream_t s, uint64_t *launches)
+{
+    if (wb.n_large == 0) return AMB_OK;
+    WealthJob *jobs = static_cast<WealthJob *>(wb.d_jobs);
+    wealth_batch_donate_kernel<<<wb.large_chunks, 256, 0, s>>>(jobs, wb.d_large, wb.d_prefix, wb.n_large);
+    wealth_batch_apply_kernel<<<wb.large_chunks, 256, 0, s>>>(jobs, wb.d_large, wb.d_prefix, wb.n_large);
+    wealth_batch_advance_kernel<<<grid_for(wb.n_large, 128), 128, 0, s>>>(jobs, wb.d_large, wb.n_large);
+    AMB_TRY_CUDA(cudaGetLastError());
+    *launches += 3;
+    return AMB_OK;
+}
+
+void wealth_batch_release(WealthBatch &wb, cudaStream_t s)
+{
+    void *j = wb.d_jobs;
+    dfree(j, s);
+    wb.d_jobs = nullptr;
+    dfree(wb.d_small, s);
+    dfree(wb.d_large, s);
+    dfree(wb.d_prefix, s);
 }
 
 // Grid-wide path, phase 1: donors on the snapshot credit their recipient.

@@ -42,6 +42,7 @@
 // the range of kmin over that byte's 2^24 values, then a binary search inside
 // the range (usually empty).
 #include <algorithm>
+#include <cstring>
 
 #include "amb_internal.cuh"
 
@@ -77,6 +78,7 @@ struct BandArgs {
     uint64_t *status;
     uint32_t epoch;
     uint32_t *err;
+    const uint32_t *code_tab;  // precomputed CodeTables (batched steps), or null
 };
 
 // Philox4x32-10 block for counter (c0, c1, 0, 0) with the ten round keys
@@ -501,66 +503,61 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kBandNT, kBandCtasPerSm) sir_band_kernel(const BandArgs a)
+// All threads: band b of the step described by `a` (its source-row tables,
+// then band_body with shared-memory or, for very dense bands, global
+// counters).  prefetch: pull band b + gridDim.x into L2 meanwhile.
+__device__ __forceinline__ void process_band(const BandArgs &a, BandShared &sh, uint32_t *band_smem,
+                                             uint32_t *wide_slice, uint32_t b, uint32_t tinf_max, bool prefetch,
+                                             Tally &tl)
 {
-    extern __shared__ __align__(16) uint32_t band_smem[];
-    __shared__ BandShared sh;
-    const uint32_t L = a.L, H = a.H;
-    const uint32_t tid = threadIdx.x;
-
-    if (blockIdx.x == 0 && tid == 0) a.tickets[a.parity ^ 1u] = 0ull;
-    if (tid < 4) sh.cnt[tid] = 0ull;
-    load_code_tables(sh.ct, a.t_inf, a.K);
-    const uint32_t tinf_max = a.t_inf[a.K];
-    Tally tl = {0u, 0u, 0u, 0u};
+    const uint32_t L = a.L, tid = threadIdx.x;
     const bool single = (a.n_bands == 1);
-    const PackedCtr packed{band_smem};
-    const WideCtr wide{a.wide ? a.wide + (size_t)blockIdx.x * 2u * H * L : nullptr,
-                       a.wide ? a.wide + (size_t)blockIdx.x * 2u * H * L + (size_t)H * L : nullptr};
-    for (;;) {
-        if (tid == 0) sh.band = (uint32_t)atomicAdd(&a.tickets[a.parity], 1ull);
-        __syncthreads();
-        const uint32_t b = sh.band;
-        if (b >= a.n_bands) break;
-        // the band the next wave of tickets is likely to give this CTA: have
-        // its records pulled into L2 while this one is processed (a guess;
-        // a wrong guess only warms L2 for another CTA)
-        const uint32_t ahead = b + gridDim.x;
-        if (tid < 32 && ahead < a.n_bands) prefetch_band(a, ahead, single);
-        // bands of floor / ceil(L / n_bands) rows
-        const uint32_t r0 = (uint32_t)(((uint64_t)b * L) / a.n_bands);
-        const uint32_t r1 = (uint32_t)(((uint64_t)(b + 1u) * L) / a.n_bands);
-        // source rows r0-1 .. r1 (all rows, once, when one band covers the grid)
-        const uint32_t nsrc = single ? L : (r1 - r0) + 2u;
-        uint32_t len = 0, beg = 0, y = 0;
-        if (tid < nsrc) {
-            y = single ? tid : (r0 + L - 1u + tid) % L;
-            const int32_t b0 = a.row_in[y], b1 = a.row_in[y + 1];
+    // the band the next wave of tickets is likely to give this CTA: have its
+    // records pulled into L2 while this one is processed (a guess; a wrong
+    // guess only warms L2 for another CTA)
+    const uint32_t ahead = b + gridDim.x;
+    if (prefetch && tid < 32 && ahead < a.n_bands) prefetch_band(a, ahead, single);
+    // bands of floor / ceil(L / n_bands) rows
+    const uint32_t r0 = (uint32_t)(((uint64_t)b * L) / a.n_bands);
+    const uint32_t r1 = (uint32_t)(((uint64_t)(b + 1u) * L) / a.n_bands);
+    // source rows r0-1 .. r1 (all rows, once, when one band covers the grid)
+    const uint32_t nsrc = single ? L : (r1 - r0) + 2u;
+    uint32_t len = 0, beg = 0, y = 0;
+    if (tid < nsrc) {
+        y = single ? tid : (r0 + L - 1u + tid) % L;
+        const int32_t b0 = a.row_in[y], b1 = a.row_in[y + 1];
+        if (b0 >= 0 && b1 >= b0 && (uint32_t)b1 <= a.n) {
             beg = (uint32_t)b0;
             len = (uint32_t)(b1 - b0);
+        } else {
+            atomicOr(a.err, ERR_RANGE);  // a corrupt row table: the row is skipped
         }
-        uint32_t M;
-        const uint32_t off = block_exclusive_scan<kBandNT>(len, sh.warp, &M);
-        if (tid < nsrc) {
-            sh.srow[tid] = off;
-            sh.sbase[tid] = beg;
-            sh.sy[tid] = y;
-            uint32_t tab = 0;
-            for (uint32_t dp = 0; dp < 3u; ++dp) {
-                const uint32_t yo = wrap_step(y, dp, L) - r0;  // wraps above 0xFF when outside
-                tab |= (yo < r1 - r0 ? yo : 0xFFu) << (8u * dp);
-            }
-            sh.ytab[tid] = tab;
-        }
-        if (tid == 0) sh.srow[nsrc] = M;
-        __syncthreads();
-        if (M < kPackedLimit || a.wide == nullptr)
-            band_body(a, sh, packed, b, r0, r1, M, tinf_max, tl);
-        else
-            band_body(a, sh, wide, b, r0, r1, M, tinf_max, tl);
     }
+    uint32_t M;
+    const uint32_t off = block_exclusive_scan<kBandNT>(len, sh.warp, &M);
+    if (tid < nsrc) {
+        sh.srow[tid] = off;
+        sh.sbase[tid] = beg;
+        sh.sy[tid] = y;
+        uint32_t tab = 0;
+        for (uint32_t dp = 0; dp < 3u; ++dp) {
+            const uint32_t yo = wrap_step(y, dp, L) - r0;  // wraps above 0xFF when outside
+            tab |= (yo < r1 - r0 ? yo : 0xFFu) << (8u * dp);
+        }
+        sh.ytab[tid] = tab;
+    }
+    if (tid == 0) sh.srow[nsrc] = M;
+    __syncthreads();
+    if (M < kPackedLimit || wide_slice == nullptr)
+        band_body(a, sh, PackedCtr{band_smem}, b, r0, r1, M, tinf_max, tl);
+    else
+        band_body(a, sh, WideCtr{wide_slice, wide_slice + (size_t)a.H * L}, b, r0, r1, M, tinf_max, tl);
+}
 
-    // per-step counts
+// All threads: add the block's tally to row[0..3] and clear it.
+__device__ __forceinline__ void flush_tally(BandShared &sh, Tally &tl, int64_t *row)
+{
+    const uint32_t tid = threadIdx.x;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         tl.s += __shfl_down_sync(0xffffffffu, tl.s, o);
@@ -575,7 +572,155 @@ __global__ void __launch_bounds__(kBandNT, kBandCtasPerSm) sir_band_kernel(const
         if (tl.fresh) atomicAdd(&sh.cnt[3], (unsigned long long)tl.fresh);
     }
     __syncthreads();
-    if (tid < 4 && sh.cnt[tid]) atomicAdd(reinterpret_cast<unsigned long long *>(&a.row[tid]), sh.cnt[tid]);
+    if (tid < 4) {
+        if (sh.cnt[tid]) atomicAdd(reinterpret_cast<unsigned long long *>(&row[tid]), sh.cnt[tid]);
+        sh.cnt[tid] = 0ull;
+    }
+    tl = Tally{0u, 0u, 0u, 0u};
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBandNT, kBandCtasPerSm) sir_band_kernel(const BandArgs a)
+{
+    extern __shared__ __align__(16) uint32_t band_smem[];
+    __shared__ BandShared sh;
+    const uint32_t tid = threadIdx.x;
+
+    if (blockIdx.x == 0 && tid == 0) a.tickets[a.parity ^ 1u] = 0ull;
+    if (tid < 4) sh.cnt[tid] = 0ull;
+    load_code_tables(sh.ct, a.t_inf, a.K);
+    const uint32_t tinf_max = a.t_inf[a.K];
+    Tally tl = {0u, 0u, 0u, 0u};
+    uint32_t *wide_slice = a.wide ? a.wide + (size_t)blockIdx.x * 2u * a.H * a.L : nullptr;
+    for (;;) {
+        if (tid == 0) sh.band = (uint32_t)atomicAdd(&a.tickets[a.parity], 1ull);
+        __syncthreads();
+        const uint32_t b = sh.band;
+        if (b >= a.n_bands) break;
+        process_band(a, sh, band_smem, wide_slice, b, tinf_max, true, tl);
+    }
+    flush_tally(sh, tl, a.row);
+}
+
+// ---------------------------------------------------------------- batch ---
+// One step of many SIR populations in one launch: tickets run over the
+// concatenation of every job's bands (job by job, band by band), so within a
+// job the bands are handed out in order and each job keeps its own look-back
+// chain (its own status words, this launch's epoch).  jobs[j] is the job's
+// step descriptor (its buffers, step, count row, code tables); a job whose
+// step has reached t_end is skipped.
+// a batched step launch gives up taking bands after this long
+constexpr uint64_t kBatchLimitNs = 4ull * kSpinLimitNs;
+
+// last job whose first band is <= g (prefix[0] = 0 <= g)
+__device__ __forceinline__ uint32_t chunk_of(const uint32_t *prefix, uint32_t n_jobs, uint32_t g)
+{
+    uint32_t lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= g)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+struct SirJob {
+    BandArgs a;
+    uint32_t t_end;
+    uint32_t pad[3];
+};
+
+__global__ void __launch_bounds__(kBandNT, kBandCtasPerSm)
+    sir_batch_kernel(const SirJob *__restrict__ jobs, const uint32_t *__restrict__ band_prefix, uint32_t n_jobs,
+                     uint32_t *wide, uint32_t wide_words, unsigned long long *tickets, uint32_t parity,
+                     uint32_t epoch)
+{
+    extern __shared__ __align__(16) uint32_t band_smem[];
+    __shared__ BandShared sh;
+    __shared__ BandArgs a;
+    __shared__ uint32_t s_job, s_prev, s_t_end;
+    __shared__ uint64_t s_t0;
+    const uint32_t tid = threadIdx.x;
+    if (tid == 0) s_t0 = global_ns();
+    if (blockIdx.x == 0 && tid == 0) tickets[parity ^ 1u] = 0ull;
+    if (tid < 4) sh.cnt[tid] = 0ull;
+    if (tid == 0) s_prev = 0xFFFFFFFFu;
+    Tally tl = {0u, 0u, 0u, 0u};
+    const uint32_t total = band_prefix[n_jobs];
+    uint32_t *wide_slice = wide ? wide + (size_t)blockIdx.x * wide_words : nullptr;
+    for (;;) {
+        if (tid == 0) {
+            uint32_t g = (uint32_t)atomicAdd(&tickets[parity], 1ull);
+            if (g < total && global_ns() - s_t0 > kBatchLimitNs) {
+                // the launch has run far longer than any step can: flag the
+                // job of this band and stop taking bands
+                const uint32_t jj = chunk_of(band_prefix, n_jobs, g);
+                atomicOr(jobs[jj].a.err, ERR_TIMEOUT);
+                g = total;
+            }
+            sh.band = g;
+            if (g < total) {
+                s_job = chunk_of(band_prefix, n_jobs, g);
+            }
+        }
+        __syncthreads();
+        const uint32_t g = sh.band;
+        if (g >= total) break;
+        const uint32_t j = s_job;
+        // the job's step descriptor, with this launch's epoch
+        constexpr uint32_t kWords = sizeof(BandArgs) / 4u;
+        if (tid < kWords) reinterpret_cast<uint32_t *>(&a)[tid] = reinterpret_cast<const uint32_t *>(&jobs[j].a)[tid];
+        if (tid == 0) s_t_end = jobs[j].t_end;
+        __syncthreads();
+        if (tid == 0) a.epoch = epoch;
+        const bool live = a.t < s_t_end;
+        if (live && j != s_prev) {
+            // the job's precomputed code tables
+            const uint32_t *src = a.code_tab;
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&sh.ct);
+            for (uint32_t i = tid; i < sizeof(CodeTables) / 4u; i += kBandNT) dst[i] = src[i];
+        }
+        __syncthreads();
+        if (live) {
+            if (tid == 0) s_prev = j;
+            const uint32_t tinf_max = a.t_inf[a.K];
+            process_band(a, sh, band_smem, wide_slice, g - band_prefix[j], tinf_max, false, tl);
+            flush_tally(sh, tl, a.row);
+        }
+        __syncthreads();
+    }
+}
+
+// After a batched step: every live job moves to its next step (buffers swap,
+// step and count row advance).
+__global__ void sir_batch_advance(SirJob *__restrict__ jobs, uint32_t n_jobs)
+{
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n_jobs; j += gridDim.x * blockDim.x) {
+        BandArgs &a = jobs[j].a;
+        if (a.t >= jobs[j].t_end) continue;
+        uint32_t *id = a.id_out, *aux = a.aux_out;
+        int32_t *row = a.row_out;
+        a.id_out = const_cast<uint32_t *>(a.id_in);
+        a.aux_out = const_cast<uint32_t *>(a.aux_in);
+        a.row_out = const_cast<int32_t *>(a.row_in);
+        a.id_in = id;
+        a.aux_in = aux;
+        a.row_in = row;
+        a.t += 1u;
+        a.row += 4;
+    }
+}
+
+// Code tables of one job (the shared-memory tables of load_code_tables) into
+// global memory, one block.
+__global__ void code_tables_kernel(const uint32_t *__restrict__ t_inf, uint32_t K, uint32_t *__restrict__ out)
+{
+    __shared__ CodeTables ct;
+    load_code_tables(ct, t_inf, K);
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(&ct);
+    for (uint32_t i = threadIdx.x; i < sizeof(CodeTables) / 4u; i += blockDim.x) out[i] = src[i];
 }
 
 // ------------------------------------------------------------- set-up ---
@@ -668,16 +813,18 @@ struct BandGeometry {
     uint32_t H, n_bands, smem;
 };
 
-static bool band_geometry(uint32_t L, uint32_t grid_max, BandGeometry *g)
+static bool band_geometry(uint32_t L, uint32_t grid_max, BandGeometry *g, uint32_t rows_cap = kMaxBandRows)
 {
     if (L < 1 || L > 0xFFFFu || (uint64_t)L * 4u > kBandSmem) return false;
+    rows_cap = std::max<uint32_t>(1u, std::min<uint32_t>(rows_cap, kMaxBandRows));
     const uint32_t by_smem = kBandSmem / (L * 4u);
     uint32_t H, nb;
-    if (L <= kMaxBandRows && L <= by_smem) {
+    if (L <= rows_cap && L <= by_smem) {
         H = L;
         nb = 1;
     } else {
-        const uint32_t h = std::min<uint32_t>(std::min<uint32_t>(kMaxBandRows, by_smem), L - 2u);
+        const uint32_t h = std::max<uint32_t>(
+            1u, std::min<uint32_t>(std::min<uint32_t>(rows_cap, by_smem), L > 2u ? L - 2u : 1u));
         const uint32_t waves = (L + grid_max * h - 1u) / (grid_max * h);
         nb = std::min<uint32_t>(L, grid_max * waves);
         H = (L + nb - 1u) / nb;
@@ -788,6 +935,7 @@ amb_status sir_band_steps(amb_pop *pop, uint32_t k)
         a.status = pop->lb.status;
         pop->lb.next(&a.parity, &a.epoch);
         a.err = pop->err;
+        a.code_tab = nullptr;
         sir_band_kernel<<<pop->band_grid, kBandNT, smem, s>>>(a);
         AMB_TRY_CUDA(cudaGetLastError());
         pop->cur = out;
@@ -823,6 +971,144 @@ void sir_band_release(amb_pop *pop)
         dfree(pop->row_start[b], pop->stream);
     }
     dfree(pop->band_wide, pop->stream);
+}
+
+}  // namespace amb
+
+namespace amb {
+
+// ------------------------------------------------------- batch, host side ---
+// Re-derive the band geometry of a population with at most rows_cap rows per
+// band (the records do not depend on it).
+static amb_status sir_band_regeometry(amb_pop *pop, uint32_t rows_cap)
+{
+    cudaStream_t s = pop->stream;
+    const uint32_t L = pop->p.grid_side;
+    const uint32_t grid_max = (uint32_t)(sm_count() * kBandCtasPerSm);
+    BandGeometry g;
+    if (!band_geometry(L, grid_max, &g, rows_cap)) return fail(AMB_EINVAL, "band path does not support L = %u", L);
+    const bool grow = (size_t)g.H * L > (size_t)pop->band_rows * L || std::min<uint32_t>(g.n_bands, grid_max) > pop->band_grid;
+    pop->band_rows = g.H;
+    pop->n_bands = g.n_bands;
+    pop->band_grid = std::min<uint32_t>(g.n_bands, grid_max);
+    pop->band_smem = g.smem;
+    if (pop->p.n >= kPackedLimit && grow) {
+        dfree(pop->band_wide, s);
+        AMB_TRY(dalloc(&pop->band_wide, (size_t)pop->band_grid * 2u * g.H * L, s));
+    }
+    AMB_TRY(pop->lb.ensure(pop->n_bands, s));
+    return AMB_OK;
+}
+
+amb_status sir_batch_build(SirBatch &sb, amb_pop **pops, const uint32_t *steps, uint32_t n, uint32_t rows_cap,
+                           cudaStream_t s)
+{
+    std::vector<SirJob> jobs(n);
+    std::vector<uint32_t> prefix((size_t)n + 1, 0u);
+    const uint32_t grid_max = (uint32_t)(sm_count() * kBandCtasPerSm);
+    uint32_t base = 0;
+    size_t smem = 16, wide_words = 0;
+    for (uint32_t q = 0; q < n; ++q) base = std::max<uint32_t>(base, pops[q]->lb.launches);
+    sb.epoch_base = base;  // batch epochs continue after every population's own
+    AMB_TRY(dalloc(&sb.d_codes, (size_t)std::max<uint32_t>(n, 1u) * 512u, s));
+    for (uint32_t q = 0; q < n; ++q) {
+        amb_pop *p = pops[q];
+        AMB_TRY(sir_band_regeometry(p, rows_cap));
+        AMB_TRY(ensure_series(p, p->t + steps[q]));
+        if (steps[q])
+            AMB_TRY_CUDA(cudaMemsetAsync(p->series + (size_t)p->t * 4u, 0, (size_t)steps[q] * 4u * sizeof(int64_t), s));
+        code_tables_kernel<<<1, 256, 0, s>>>(p->t_inf_d, p->K, sb.d_codes + (size_t)q * 512u);
+        AMB_TRY_CUDA(cudaGetLastError());
+        BandArgs &a = jobs[q].a;
+        memset(&a, 0, sizeof(a));
+        const int in = p->cur, out = p->cur ^ 1;
+        a.id_in = p->rec_id[in];
+        a.aux_in = p->rec_aux[in];
+        a.row_in = p->row_start[in];
+        a.id_out = p->rec_id[out];
+        a.aux_out = p->rec_aux[out];
+        a.row_out = p->row_start[out];
+        a.start = p->start;
+        a.wide = nullptr;
+        a.n = p->p.n;
+        a.L = p->p.grid_side;
+        a.H = p->band_rows;
+        a.n_bands = p->n_bands;
+        a.k0 = p->key0;
+        a.k1 = p->key1;
+        a.t = (uint32_t)p->t;
+        round_keys(p->key0, p->key1, a.rk0, a.rk1);
+        a.t_inf = p->t_inf_d;
+        a.K = p->K;
+        a.t_rec = p->t_rec;
+        a.row = p->series + (size_t)p->t * 4u;
+        a.status = p->lb.status;
+        a.err = p->err;
+        a.code_tab = sb.d_codes + (size_t)q * 512u;
+        jobs[q].t_end = (uint32_t)(p->t + steps[q]);
+        const bool live = steps[q] > 0 && p->p.n > 0;
+        prefix[q + 1] = prefix[q] + (live ? p->n_bands : 0u);
+        smem = std::max<size_t>(smem, p->band_smem);
+        if (p->p.n >= kPackedLimit) wide_words = std::max<size_t>(wide_words, (size_t)2u * p->band_rows * a.L);
+    }
+    sb.n_jobs = n;
+    sb.total_bands = prefix[n];
+    sb.grid = std::max<uint32_t>(1u, std::min<uint32_t>(sb.total_bands, grid_max));
+    sb.smem = smem;
+    sb.wide_words = (uint32_t)wide_words;
+    AMB_TRY(dalloc(reinterpret_cast<unsigned char **>(&sb.d_jobs), (size_t)std::max<uint32_t>(n, 1u) * sizeof(SirJob), s));
+    AMB_TRY(dalloc(&sb.d_prefix, (size_t)n + 1, s));
+    AMB_TRY(dalloc(&sb.tickets, 2, s));
+    AMB_TRY_CUDA(cudaMemsetAsync(sb.tickets, 0, 2 * sizeof(unsigned long long), s));
+    if (wide_words) AMB_TRY(dalloc(&sb.wide, (size_t)sb.grid * wide_words, s));
+    if (n) AMB_TRY_CUDA(cudaMemcpyAsync(sb.d_jobs, jobs.data(), (size_t)n * sizeof(SirJob), cudaMemcpyHostToDevice, s));
+    AMB_TRY_CUDA(cudaMemcpyAsync(sb.d_prefix, prefix.data(), prefix.size() * 4u, cudaMemcpyHostToDevice, s));
+    AMB_TRY_CUDA(cudaFuncSetAttribute(sir_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb.smem));
+    AMB_TRY_CUDA(cudaStreamSynchronize(s));  // the host tables go out of scope
+    sb.launches = 0;
+    return AMB_OK;
+}
+
+amb_status sir_batch_step(SirBatch &sb, cudaStream_t s, uint64_t *launches)
+{
+    if (sb.total_bands == 0) return AMB_OK;
+    const uint32_t k = sb.epoch_base + sb.launches;
+    const uint32_t parity = sb.launches & 1u;
+    const uint32_t epoch = (k % 0x3FFFFFFFu) + 1u;
+    ++sb.launches;
+    sir_batch_kernel<<<sb.grid, kBandNT, sb.smem, s>>>(static_cast<const SirJob *>(sb.d_jobs), sb.d_prefix, sb.n_jobs,
+                                                        sb.wide, sb.wide_words, sb.tickets, parity, epoch);
+    sir_batch_advance<<<grid_for(sb.n_jobs, 128), 128, 0, s>>>(static_cast<SirJob *>(sb.d_jobs), sb.n_jobs);
+    AMB_TRY_CUDA(cudaGetLastError());
+    *launches += 2;
+    return AMB_OK;
+}
+
+void sir_batch_finish(SirBatch &sb, amb_pop **pops, const uint32_t *steps, uint32_t n)
+{
+    for (uint32_t q = 0; q < n; ++q) {
+        amb_pop *p = pops[q];
+        p->t += steps[q];
+        if (steps[q] & 1u) p->cur ^= 1;
+        // later epochs must exceed the batch's, and the launch parity must
+        // continue the population's own alternation of ticket counters (the
+        // counter of the parity it used last is the one not reset)
+        uint32_t next = std::max<uint32_t>(p->lb.launches, sb.epoch_base + sb.launches);
+        if ((next ^ p->lb.launches) & 1u) ++next;
+        p->lb.launches = next;
+        p->launches += steps[q];
+    }
+}
+
+void sir_batch_release(SirBatch &sb, cudaStream_t s)
+{
+    void *j = sb.d_jobs;
+    dfree(j, s);
+    sb.d_jobs = nullptr;
+    dfree(sb.d_prefix, s);
+    dfree(sb.d_codes, s);
+    dfree(sb.wide, s);
+    dfree(sb.tickets, s);
 }
 
 }  // namespace amb
