@@ -236,6 +236,46 @@ def run_e2e(amb, torch, steps, rank, stream):
             "d2h_bytes_per_step": d2h / steps, "seconds": t1 - t0}
 
 
+def sweep_bench(amb, torch, stream, rank, world):
+    """The parameter sweep (1,024 wealth / SIR replicates, 200 steps each;
+    ranks split the job list): one batch, graph-captured and autotuned, against
+    the same jobs stepped one at a time through amb_step on the same GPU."""
+    from paper_2601_16292_gb300 import workloads
+    jobs = workloads.sweep_jobs()[rank::world]
+    total = workloads.agent_steps(jobs)
+    b = amb.Batch(jobs, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ms = b.run(autotune=True)
+    wall = time.perf_counter() - t0
+    info = b.info()
+    b.close()
+    # one job at a time: create, step all its steps, read its counts, destroy
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dev_ms = 0.0
+    launches = 0
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for j in jobs:
+        kw = {k: v for k, v in j.items() if k not in ("model", "steps")}
+        p = amb.Population(j["model"], stream=stream, **kw)
+        e0.record(stream)
+        amb.amb_step(p.handle, j["steps"])
+        e1.record(stream)
+        p.counts()
+        e1.synchronize()
+        dev_ms += e0.elapsed_time(e1)
+        launches += amb.amb_launch_count(p.handle)
+        p.close()
+    wall_one = time.perf_counter() - t1
+    return {"jobs": len(jobs), "agent_steps": total,
+            "batched": {"value": total / (ms / 1e3), "device_ms": ms, "wall_s": wall, "launches": info["launches"],
+                        "band_rows_cap": info["band_rows_cap"], "spread_bands": info["spread_bands"]},
+            "one_at_a_time": {"value": total / (dev_ms / 1e3), "device_ms": dev_ms, "wall_s": wall_one,
+                              "wall_value": total / wall_one, "launches": launches},
+            "speedup_device": dev_ms / ms, "unit": "agent-steps/s"}
+
+
 def cpu_baseline(budget_s=15.0):
     """The oracle as it stands on one host core: the full 10M-agent SIR
     population, as many whole steps as fit in the budget (at least one)."""
@@ -267,6 +307,7 @@ def gpu_arm(args):
     only_sir = args.only == "sir"
     wealth = None if only_sir else time_model_block(amb, torch, "wealth", WEALTH_CFG, stream, rank)
     walk = None if only_sir else time_model_block(amb, torch, "walk", WALK_CFG, stream, rank)
+    sweep = None if only_sir else sweep_bench(amb, torch, stream, rank, world)
 
     sampler = ClockSampler(local)
     barrier(world)
@@ -328,6 +369,7 @@ def gpu_arm(args):
         "clocks": clocks,
         "invariants_ok": bool(inv["ok"]),
         "models": {"wealth_10k_100steps": wealth, "walk_1M_L1000_200steps": walk},
+        "sweep_1024_jobs": sweep,
     }
     print(json.dumps(line))
     if world > 1:
@@ -382,11 +424,17 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="amb", choices=["amb", "reference"])
-    ap.add_argument("--only", default="all", choices=["all", "sir"],
-                    help="sir: time the SIR step alone (no extras; for profiling)")
+    ap.add_argument("--only", default="all", choices=["all", "sir", "sweep"],
+                    help="sir: time the SIR step alone (no extras; for profiling); sweep: the sweep alone")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.impl == "amb" and args.only == "sweep":
+        import torch
+        from paper_2601_16292_gb300 import amb
+        torch.cuda.set_device(0)
+        print(json.dumps(sweep_bench(amb, torch, torch.cuda.Stream(), 0, 1)))
+        return
     if args.impl == "reference":
         reference_arm(args)
     else:

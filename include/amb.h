@@ -241,14 +241,18 @@ typedef struct {
 
 typedef struct {
     uint32_t band_rows_cap; /* tallest SIR band in rows (1..32); 0 = 32 */
-    int32_t autotune;       /* 1: time caps 8, 16, 32 on throwaway copies of up to eight
-                               of the largest SIR jobs and keep the fastest */
+    int32_t spread_bands;   /* 0: each SIR job in the fewest bands (many jobs share the GPU);
+                               1: each job's bands spread over every SM */
+    int32_t autotune;       /* 1: time the shapes {8, 16, 32 rows} x {fewest, spread} on
+                               throwaway copies of up to eight of the largest SIR jobs and
+                               keep the fastest (overrides the two fields above) */
     int32_t use_graph;      /* 1: one CUDA graph for the whole run */
 } amb_tune;
 
 typedef struct {
     size_t n_jobs;
-    uint32_t band_rows_cap; /* the cap used */
+    uint32_t band_rows_cap; /* the band shape used */
+    int32_t spread_bands;
     uint64_t launches;      /* kernel launches of the run */
     uint64_t agent_steps;   /* sum over jobs of n * steps */
     double ms;              /* device time of the run (events around the graph launch) */

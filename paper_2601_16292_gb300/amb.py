@@ -59,11 +59,13 @@ class amb_job(ctypes.Structure):
 
 
 class amb_tune(ctypes.Structure):
-    _fields_ = [("band_rows_cap", ctypes.c_uint32), ("autotune", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+    _fields_ = [("band_rows_cap", ctypes.c_uint32), ("spread_bands", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32)]
 
 
 class amb_batch_report(ctypes.Structure):
-    _fields_ = [("n_jobs", ctypes.c_size_t), ("band_rows_cap", ctypes.c_uint32), ("launches", ctypes.c_uint64),
+    _fields_ = [("n_jobs", ctypes.c_size_t), ("band_rows_cap", ctypes.c_uint32), ("spread_bands", ctypes.c_int32),
+                ("launches", ctypes.c_uint64),
                 ("agent_steps", ctypes.c_uint64), ("ms", ctypes.c_double)]
 
 
@@ -298,8 +300,9 @@ def amb_batch_create(jobs, stream=None):
     return h
 
 
-def amb_batch_run(batch, band_rows_cap=0, autotune=False, use_graph=True):
-    t = amb_tune(band_rows_cap=int(band_rows_cap), autotune=int(bool(autotune)), use_graph=int(bool(use_graph)))
+def amb_batch_run(batch, band_rows_cap=0, autotune=False, use_graph=True, spread_bands=False):
+    t = amb_tune(band_rows_cap=int(band_rows_cap), spread_bands=int(bool(spread_bands)), autotune=int(bool(autotune)),
+                 use_graph=int(bool(use_graph)))
     ms = ctypes.c_double()
     _check(lib().amb_batch_run(batch, ctypes.byref(t), ctypes.byref(ms)))
     return ms.value
@@ -414,8 +417,8 @@ class Batch:
         self.specs = [dict(j) for j in jobs]
         self.handle = amb_batch_create([make_job(**j) for j in self.specs], stream)
 
-    def run(self, band_rows_cap=0, autotune=False, use_graph=True):
-        return amb_batch_run(self.handle, band_rows_cap, autotune, use_graph)
+    def run(self, band_rows_cap=0, autotune=False, use_graph=True, spread_bands=False):
+        return amb_batch_run(self.handle, band_rows_cap, autotune, use_graph, spread_bands)
 
     def info(self):
         return amb_batch_info(self.handle)

@@ -103,7 +103,13 @@ struct SirBatch {
     uint32_t epoch_base = 0, launches = 0;
     size_t smem = 0;
 };
-amb_status sir_batch_build(SirBatch &sb, amb_pop **pops, const uint32_t *steps, uint32_t n, uint32_t rows_cap,
+// Band shape of the populations in a batch: rows per band at most rows_cap;
+// spread = as many bands as fill the GPU, else the fewest bands.
+struct BandShape {
+    uint32_t rows_cap = 32;
+    bool spread = false;
+};
+amb_status sir_batch_build(SirBatch &sb, amb_pop **pops, const uint32_t *steps, uint32_t n, BandShape shape,
                            cudaStream_t s);
 amb_status sir_batch_step(SirBatch &sb, cudaStream_t s, uint64_t *launches);
 // hand the populations back to single stepping after `steps[q]` batched steps

@@ -23,7 +23,7 @@ struct amb_batch {
     std::vector<amb_job> jobs;
     std::vector<amb_pop *> pops;
     bool ran = false;
-    uint32_t rows_cap = 0;
+    BandShape shape;
     uint64_t launches = 0;
     double ms = 0.0;
 };
@@ -66,13 +66,13 @@ amb_status check_errors(const std::vector<amb_pop *> &pops, cudaStream_t s)
     return AMB_OK;
 }
 
-// Batched SIR steps of `pops` with the given cap: `steps` steps, timed on s.
-amb_status time_sir(std::vector<amb_pop *> &pops, uint32_t steps, uint32_t cap, cudaStream_t s, float *ms)
+// Batched SIR steps of `pops` with the given band shape: `steps` steps, timed on s.
+amb_status time_sir(std::vector<amb_pop *> &pops, uint32_t steps, BandShape shape, cudaStream_t s, float *ms)
 {
     std::vector<uint32_t> st(pops.size(), steps);
     SirBatch sb;
     uint64_t launches = 0;
-    amb_status r = sir_batch_build(sb, pops.data(), st.data(), (uint32_t)pops.size(), cap, s);
+    amb_status r = sir_batch_build(sb, pops.data(), st.data(), (uint32_t)pops.size(), shape, s);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (r == AMB_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         r = fail(AMB_ECUDA, "event creation failed");
@@ -90,33 +90,38 @@ amb_status time_sir(std::vector<amb_pop *> &pops, uint32_t steps, uint32_t cap, 
     return r;
 }
 
-// Band-height cap with the shortest batched SIR step on throwaway copies of
-// (up to) the eight largest SIR jobs.
-amb_status autotune_rows_cap(const std::vector<amb_job> &jobs, cudaStream_t s, uint32_t *cap)
+// Band shape with the shortest batched SIR step on throwaway copies of (up
+// to) the eight largest SIR jobs: caps of 8, 16 and 32 rows, fewest or spread
+// bands.
+amb_status autotune_shape(const std::vector<amb_job> &jobs, cudaStream_t s, BandShape *best_shape)
 {
     std::vector<size_t> sir;
     for (size_t i = 0; i < jobs.size(); ++i)
         if (jobs[i].model == AMB_SIR && jobs[i].params.n > 0 && jobs[i].steps > 0) sir.push_back(i);
-    *cap = 32;
+    *best_shape = BandShape{};
     if (sir.empty()) return AMB_OK;
     std::sort(sir.begin(), sir.end(), [&](size_t a, size_t b) { return jobs[a].params.n > jobs[b].params.n; });
     if (sir.size() > 8) sir.resize(8);
     std::vector<amb_job> sample;
     for (size_t i : sir) sample.push_back(jobs[i]);
-    const uint32_t cands[] = {8, 16, 32};
     float best = 1e30f;
-    for (uint32_t c : cands) {
-        std::vector<amb_pop *> pops;
-        AMB_TRY(create_pops(sample.data(), sample.size(), s, pops));
-        float warm = 0.f, ms = 0.f;
-        amb_status r = time_sir(pops, 1, c, s, &warm);
-        if (r == AMB_OK) r = time_sir(pops, 3, c, s, &ms);
-        if (r == AMB_OK) r = check_errors(pops, s);
-        destroy_pops(pops);
-        AMB_TRY(r);
-        if (ms < best) {
-            best = ms;
-            *cap = c;
+    for (int spread = 0; spread < 2; ++spread) {
+        for (uint32_t c : {8u, 16u, 32u}) {
+            BandShape shape;
+            shape.rows_cap = c;
+            shape.spread = spread != 0;
+            std::vector<amb_pop *> pops;
+            AMB_TRY(create_pops(sample.data(), sample.size(), s, pops));
+            float warm = 0.f, ms = 0.f;
+            amb_status r = time_sir(pops, 1, shape, s, &warm);
+            if (r == AMB_OK) r = time_sir(pops, 3, shape, s, &ms);
+            if (r == AMB_OK) r = check_errors(pops, s);
+            destroy_pops(pops);
+            AMB_TRY(r);
+            if (ms < best) {
+                best = ms;
+                *best_shape = shape;
+            }
         }
     }
     return AMB_OK;
@@ -151,10 +156,12 @@ amb_status amb_batch_run(amb_batch *b, const amb_tune *tune, double *ms_out)
     if (!b) return fail(AMB_EINVAL, "null batch");
     if (b->ran) return fail(AMB_EINVAL, "a batch runs once");
     cudaStream_t s = b->stream;
-    uint32_t cap = (tune && tune->band_rows_cap) ? tune->band_rows_cap : 32u;
+    BandShape shape;
+    if (tune && tune->band_rows_cap) shape.rows_cap = std::min<uint32_t>(tune->band_rows_cap, 32u);
+    shape.spread = tune && tune->spread_bands;
     const bool graph = !tune || tune->use_graph;
-    if (tune && tune->autotune) AMB_TRY(autotune_rows_cap(b->jobs, s, &cap));
-    b->rows_cap = cap;
+    if (tune && tune->autotune) AMB_TRY(autotune_shape(b->jobs, s, &shape));
+    b->shape = shape;
     std::vector<amb_pop *> sir, wealth, walk;
     std::vector<uint32_t> sir_steps, wealth_steps, walk_steps_v;
     uint32_t max_large = 0, max_sir = 0;
@@ -179,7 +186,7 @@ amb_status amb_batch_run(amb_batch *b, const amb_tune *tune, double *ms_out)
     }
     SirBatch sb;
     WealthBatch wb;
-    amb_status r = sir_batch_build(sb, sir.data(), sir_steps.data(), (uint32_t)sir.size(), cap, s);
+    amb_status r = sir_batch_build(sb, sir.data(), sir_steps.data(), (uint32_t)sir.size(), shape, s);
     if (r == AMB_OK) r = wealth_batch_build(wb, wealth.data(), wealth_steps.data(), (uint32_t)wealth.size(), s);
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ge = nullptr;
@@ -261,7 +268,8 @@ amb_status amb_batch_info(amb_batch *b, amb_batch_report *info)
 {
     if (!b || !info) return fail(AMB_EINVAL, "null pointer");
     info->n_jobs = b->pops.size();
-    info->band_rows_cap = b->rows_cap;
+    info->band_rows_cap = b->shape.rows_cap;
+    info->spread_bands = b->shape.spread ? 1 : 0;
     info->launches = b->launches;
     info->ms = b->ms;
     uint64_t as = 0;

@@ -813,20 +813,30 @@ struct BandGeometry {
     uint32_t H, n_bands, smem;
 };
 
-static bool band_geometry(uint32_t L, uint32_t grid_max, BandGeometry *g, uint32_t rows_cap = kMaxBandRows)
+// Band geometry of an L x L grid: single band when the whole grid fits,
+// else bands of at most min(rows_cap, smem, L - 2) rows (L - 2 keeps a band's
+// rows + 2 source rows distinct).  spread: as many bands as fill grid_max CTAs
+// (the whole GPU works on one population); otherwise the fewest bands (many
+// populations share the GPU in a batch).
+static bool band_geometry(uint32_t L, uint32_t grid_max, BandGeometry *g, uint32_t rows_cap = kMaxBandRows,
+                          bool spread = true)
 {
     if (L < 1 || L > 0xFFFFu || (uint64_t)L * 4u > kBandSmem) return false;
     rows_cap = std::max<uint32_t>(1u, std::min<uint32_t>(rows_cap, kMaxBandRows));
     const uint32_t by_smem = kBandSmem / (L * 4u);
     uint32_t H, nb;
-    if (L <= rows_cap && L <= by_smem) {
+    if ((L <= rows_cap || L <= 2u) && L <= by_smem) {
         H = L;
         nb = 1;
     } else {
         const uint32_t h = std::max<uint32_t>(
             1u, std::min<uint32_t>(std::min<uint32_t>(rows_cap, by_smem), L > 2u ? L - 2u : 1u));
-        const uint32_t waves = (L + grid_max * h - 1u) / (grid_max * h);
-        nb = std::min<uint32_t>(L, grid_max * waves);
+        if (spread) {
+            const uint32_t waves = (L + grid_max * h - 1u) / (grid_max * h);
+            nb = std::min<uint32_t>(L, grid_max * waves);
+        } else {
+            nb = (L + h - 1u) / h;
+        }
         H = (L + nb - 1u) / nb;
     }
     g->H = H;
@@ -980,13 +990,14 @@ namespace amb {
 // ------------------------------------------------------- batch, host side ---
 // Re-derive the band geometry of a population with at most rows_cap rows per
 // band (the records do not depend on it).
-static amb_status sir_band_regeometry(amb_pop *pop, uint32_t rows_cap)
+static amb_status sir_band_regeometry(amb_pop *pop, BandShape shape)
 {
     cudaStream_t s = pop->stream;
     const uint32_t L = pop->p.grid_side;
     const uint32_t grid_max = (uint32_t)(sm_count() * kBandCtasPerSm);
     BandGeometry g;
-    if (!band_geometry(L, grid_max, &g, rows_cap)) return fail(AMB_EINVAL, "band path does not support L = %u", L);
+    if (!band_geometry(L, grid_max, &g, shape.rows_cap, shape.spread))
+        return fail(AMB_EINVAL, "band path does not support L = %u", L);
     const bool grow = (size_t)g.H * L > (size_t)pop->band_rows * L || std::min<uint32_t>(g.n_bands, grid_max) > pop->band_grid;
     pop->band_rows = g.H;
     pop->n_bands = g.n_bands;
@@ -1000,7 +1011,7 @@ static amb_status sir_band_regeometry(amb_pop *pop, uint32_t rows_cap)
     return AMB_OK;
 }
 
-amb_status sir_batch_build(SirBatch &sb, amb_pop **pops, const uint32_t *steps, uint32_t n, uint32_t rows_cap,
+amb_status sir_batch_build(SirBatch &sb, amb_pop **pops, const uint32_t *steps, uint32_t n, BandShape shape,
                            cudaStream_t s)
 {
     std::vector<SirJob> jobs(n);
@@ -1013,7 +1024,7 @@ amb_status sir_batch_build(SirBatch &sb, amb_pop **pops, const uint32_t *steps, 
     AMB_TRY(dalloc(&sb.d_codes, (size_t)std::max<uint32_t>(n, 1u) * 512u, s));
     for (uint32_t q = 0; q < n; ++q) {
         amb_pop *p = pops[q];
-        AMB_TRY(sir_band_regeometry(p, rows_cap));
+        AMB_TRY(sir_band_regeometry(p, shape));
         AMB_TRY(ensure_series(p, p->t + steps[q]));
         if (steps[q])
             AMB_TRY_CUDA(cudaMemsetAsync(p->series + (size_t)p->t * 4u, 0, (size_t)steps[q] * 4u * sizeof(int64_t), s));

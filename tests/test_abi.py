@@ -63,3 +63,35 @@ def test_params_struct_layout():
     assert ctypes.sizeof(amb.amb_params) == 40
     assert ctypes.sizeof(amb.amb_invariant_report) == 40
     assert amb.amb_stats.max_occupancy.offset == 96
+
+
+def _c_layout(tmp_path, structs):
+    """sizeof and field offsets of the header's structs, as gcc lays them out."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "amb.h"', "int main(void) {"]
+    for name, cls in structs:
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))
+        for f, _ in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, f, name, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", INCLUDE, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    return {k: int(v) for k, v in (line.split() for line in out.splitlines())}
+
+
+def test_binding_structs_match_header_layout(tmp_path):
+    structs = [(n, getattr(amb, n)) for n in ("amb_params", "amb_invariant_report", "amb_stats", "amb_job", "amb_tune",
+                                              "amb_batch_report")]
+    structs += [(n, getattr(amb, n)) for n in ("amb_server_config", "amb_result", "amb_server_report")
+                if hasattr(amb, n)]
+    c = _c_layout(tmp_path, structs)
+    for name, cls in structs:
+        assert c[name] == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert c["%s.%s" % (name, f)] == getattr(cls, f).offset, (name, f)
