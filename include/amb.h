@@ -277,6 +277,92 @@ amb_status amb_batch_info(amb_batch *b, amb_batch_report *info);
 /* Free every population of the batch. */
 amb_status amb_batch_destroy(amb_batch *b);
 
+/* Device memory one job needs (host-only arithmetic, no GPU call):
+ * *resident = what its population holds while it exists (columns or
+ * cell-ordered records, cell index, thresholds, count rows, look-back words),
+ * *transient = what its creation holds on top for a moment (initial columns and
+ * counting-sort scratch).  Stream-ordered pool rounding is not included. */
+amb_status amb_job_bytes(const amb_job *job, size_t *resident, size_t *transient);
+
+/* ------------------------------------------------------------ serving ----
+ * A request loop for simulation jobs (the paper's Experiment runs, re-cast as
+ * a service; the paper has no server).  Jobs are submitted at any time from
+ * any thread.  A worker thread admits them in arrival order while their device
+ * memory (amb_job_bytes) fits the budget, keeps every admitted job's state on
+ * the device, and advances all admitted jobs together, chunk_steps steps at a
+ * time, with the batched launches (continuous batching: jobs that arrive
+ * while others run join at the next chunk; finished jobs leave and free their
+ * memory).  A job's results are bit-identical to stepping it alone.
+ */
+typedef struct {
+    size_t hbm_budget_bytes; /* device memory for job state (resident + the creation
+                                transient of the job being admitted) */
+    uint32_t max_active;     /* jobs on the device at once; 0 = 4096 */
+    uint32_t chunk_steps;    /* steps per job per iteration; 0 = 32 */
+    uint32_t band_rows_cap;  /* SIR band shape (as in amb_tune); 0 = 16 */
+    int32_t spread_bands;
+} amb_server_config;
+
+typedef struct {
+    uint64_t ticket;
+    amb_status status;     /* AMB_OK, or the error that ended the job */
+    amb_model model;
+    uint32_t n;
+    uint32_t steps;        /* steps completed */
+    int64_t last[4];       /* the job's last per-step count row (zeros when steps = 0) */
+    double submit_s;       /* host times in seconds since amb_server_create */
+    double admit_s;        /* state created on the device */
+    double done_s;         /* result readable */
+} amb_result;
+
+typedef struct {
+    uint64_t submitted, admitted, completed, failed;
+    uint64_t agent_steps;  /* of completed jobs */
+    uint64_t iterations, launches;
+    size_t hbm_in_use, hbm_peak; /* by amb_job_bytes accounting */
+    uint32_t active, pending;
+    double busy_s;         /* worker time spent advancing jobs */
+} amb_server_report;
+
+typedef struct amb_server amb_server;
+
+/* Start a server on cuda_stream (not the legacy default stream) of the
+ * current device.  cfg may not be NULL; hbm_budget_bytes > 0. */
+amb_status amb_server_create(const amb_server_config *cfg, void *cuda_stream, amb_server **out);
+
+/* Queue a job; *ticket identifies it.  keep_columns != 0 keeps the final
+ * columns on the host for amb_server_read_column.  AMB_EBUDGET when the job
+ * alone can never fit the budget; AMB_EINVAL for parameters amb_create would
+ * reject (SIR variant GENERIC included). */
+amb_status amb_server_submit(amb_server *s, const amb_job *job, int keep_columns, uint64_t *ticket);
+
+/* AMB_OK and *out filled once the job is done (out->status tells whether it
+ * succeeded); AMB_EBUSY while it is queued or running; AMB_ENOTFOUND for an
+ * unknown or released ticket. */
+amb_status amb_server_poll(amb_server *s, uint64_t ticket, amb_result *out);
+
+/* As poll, but waits up to timeout_s seconds (AMB_ETIMEOUT if still running). */
+amb_status amb_server_wait(amb_server *s, uint64_t ticket, double timeout_s, amb_result *out);
+
+/* The finished job's per-step count rows (host copy; as amb_counts). */
+amb_status amb_server_counts(amb_server *s, uint64_t ticket, int64_t *out, size_t cap_rows, size_t *rows_out);
+
+/* A kept final column of a finished job, in id order, into host memory dst
+ * (n = the job's n elements; int32, or uint8 for the state). */
+amb_status amb_server_read_column(amb_server *s, uint64_t ticket, amb_col col, void *dst, size_t n);
+
+/* Forget a finished job's result (its ticket becomes unknown). */
+amb_status amb_server_release(amb_server *s, uint64_t ticket);
+
+/* Wait until every submitted job is done (AMB_ETIMEOUT after timeout_s). */
+amb_status amb_server_drain(amb_server *s, double timeout_s);
+
+amb_status amb_server_stats(amb_server *s, amb_server_report *out);
+
+/* Stop the worker after its current iteration, cancel queued jobs, free every
+ * job's device memory and the server. */
+amb_status amb_server_destroy(amb_server *s);
+
 /*
  * amb_cell_index without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate

@@ -69,6 +69,24 @@ class amb_batch_report(ctypes.Structure):
                 ("agent_steps", ctypes.c_uint64), ("ms", ctypes.c_double)]
 
 
+class amb_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_active", ctypes.c_uint32),
+                ("chunk_steps", ctypes.c_uint32), ("band_rows_cap", ctypes.c_uint32), ("spread_bands", ctypes.c_int32)]
+
+
+class amb_result(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int), ("model", ctypes.c_int), ("n", ctypes.c_uint32),
+                ("steps", ctypes.c_uint32), ("last", ctypes.c_int64 * 4), ("submit_s", ctypes.c_double),
+                ("admit_s", ctypes.c_double), ("done_s", ctypes.c_double)]
+
+
+class amb_server_report(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("agent_steps", ctypes.c_uint64), ("iterations", ctypes.c_uint64),
+                ("launches", ctypes.c_uint64), ("hbm_in_use", ctypes.c_size_t), ("hbm_peak", ctypes.c_size_t),
+                ("active", ctypes.c_uint32), ("pending", ctypes.c_uint32), ("busy_s", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -107,6 +125,17 @@ def lib():
             "amb_batch_population": (st, [vp, sz, ctypes.POINTER(vp)]),
             "amb_batch_info": (st, [vp, ctypes.POINTER(amb_batch_report)]),
             "amb_batch_destroy": (st, [vp]),
+            "amb_job_bytes": (st, [ctypes.POINTER(amb_job), ctypes.POINTER(sz), ctypes.POINTER(sz)]),
+            "amb_server_create": (st, [ctypes.POINTER(amb_server_config), vp, ctypes.POINTER(vp)]),
+            "amb_server_submit": (st, [vp, ctypes.POINTER(amb_job), ctypes.c_int, ctypes.POINTER(u64)]),
+            "amb_server_poll": (st, [vp, u64, ctypes.POINTER(amb_result)]),
+            "amb_server_wait": (st, [vp, u64, ctypes.c_double, ctypes.POINTER(amb_result)]),
+            "amb_server_counts": (st, [vp, u64, vp, sz, ctypes.POINTER(sz)]),
+            "amb_server_read_column": (st, [vp, u64, ctypes.c_int, vp, sz]),
+            "amb_server_release": (st, [vp, u64]),
+            "amb_server_drain": (st, [vp, ctypes.c_double]),
+            "amb_server_stats": (st, [vp, ctypes.POINTER(amb_server_report)]),
+            "amb_server_destroy": (st, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -324,6 +353,83 @@ def amb_batch_destroy(batch):
     _check(lib().amb_batch_destroy(batch))
 
 
+def amb_job_bytes(job):
+    """(resident, transient) device bytes of a job (host arithmetic only)."""
+    r, t = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().amb_job_bytes(ctypes.byref(job), ctypes.byref(r), ctypes.byref(t)))
+    return r.value, t.value
+
+
+def _result_dict(r):
+    return {"ticket": r.ticket, "status": r.status, "model": r.model, "n": r.n, "steps": r.steps,
+            "last": list(r.last), "submit_s": r.submit_s, "admit_s": r.admit_s, "done_s": r.done_s}
+
+
+def amb_server_create(hbm_budget_bytes, stream, max_active=0, chunk_steps=0, band_rows_cap=0, spread_bands=False):
+    cfg = amb_server_config(hbm_budget_bytes=int(hbm_budget_bytes), max_active=int(max_active),
+                            chunk_steps=int(chunk_steps), band_rows_cap=int(band_rows_cap),
+                            spread_bands=int(bool(spread_bands)))
+    h = ctypes.c_void_p()
+    _check(lib().amb_server_create(ctypes.byref(cfg), _stream_handle(stream), ctypes.byref(h)))
+    return h
+
+
+def amb_server_submit(server, job, keep_columns=False):
+    t = ctypes.c_uint64()
+    _check(lib().amb_server_submit(server, ctypes.byref(job), int(bool(keep_columns)), ctypes.byref(t)))
+    return t.value
+
+
+def amb_server_poll(server, ticket):
+    """Result dict, or None while the job is queued or running."""
+    r = amb_result()
+    rc = lib().amb_server_poll(server, int(ticket), ctypes.byref(r))
+    if rc == AMB_EBUSY:
+        return None
+    _check(rc)
+    return _result_dict(r)
+
+
+def amb_server_wait(server, ticket, timeout_s=60.0):
+    r = amb_result()
+    _check(lib().amb_server_wait(server, int(ticket), float(timeout_s), ctypes.byref(r)))
+    return _result_dict(r)
+
+
+def amb_server_counts(server, ticket, steps):
+    out = np.zeros((max(int(steps), 1), 4), dtype=np.int64)
+    rows = ctypes.c_size_t()
+    _check(lib().amb_server_counts(server, int(ticket), ctypes.c_void_p(out.ctypes.data), int(steps),
+                                   ctypes.byref(rows)))
+    return out[:rows.value]
+
+
+def amb_server_read_column(server, ticket, col, n):
+    if isinstance(col, str):
+        col = COLUMNS[col]
+    out = np.zeros(int(n), dtype=np.uint8 if col == AMB_COL_STATE else np.int32)
+    _check(lib().amb_server_read_column(server, int(ticket), int(col), ctypes.c_void_p(out.ctypes.data), int(n)))
+    return out
+
+
+def amb_server_release(server, ticket):
+    _check(lib().amb_server_release(server, int(ticket)))
+
+
+def amb_server_drain(server, timeout_s=600.0):
+    _check(lib().amb_server_drain(server, float(timeout_s)))
+
+
+def amb_server_stats(server):
+    r = amb_server_report()
+    _check(lib().amb_server_stats(server, ctypes.byref(r)))
+    return {f: getattr(r, f) for f, _ in amb_server_report._fields_}
+
+
+def amb_server_destroy(server):
+    _check(lib().amb_server_destroy(server))
+
+
 # --------------------------------------------------------------- convenience --
 class Population:
     """Owning wrapper around an amb_pop handle (torch tensors for columns)."""
@@ -430,6 +536,52 @@ class Batch:
     def close(self):
         if self.handle is not None and self.handle.value:
             amb_batch_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Owning wrapper around amb_server; jobs are dicts of make_job keywords."""
+
+    def __init__(self, hbm_budget_bytes, stream, **cfg):
+        self.handle = amb_server_create(hbm_budget_bytes, stream, **cfg)
+        self.specs = {}
+
+    def submit(self, job, keep_columns=False):
+        t = amb_server_submit(self.handle, make_job(**job), keep_columns)
+        self.specs[t] = dict(job)
+        return t
+
+    def poll(self, ticket):
+        return amb_server_poll(self.handle, ticket)
+
+    def wait(self, ticket, timeout_s=60.0):
+        return amb_server_wait(self.handle, ticket, timeout_s)
+
+    def counts(self, ticket):
+        return amb_server_counts(self.handle, ticket, self.specs[ticket]["steps"])
+
+    def column(self, ticket, name):
+        return amb_server_read_column(self.handle, ticket, name, self.specs[ticket]["n"])
+
+    def release(self, ticket):
+        amb_server_release(self.handle, ticket)
+        self.specs.pop(ticket, None)
+
+    def drain(self, timeout_s=600.0):
+        amb_server_drain(self.handle, timeout_s)
+
+    def stats(self):
+        return amb_server_stats(self.handle)
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            amb_server_destroy(self.handle)
         self.handle = None
 
     def __del__(self):

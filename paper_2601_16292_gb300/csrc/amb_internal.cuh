@@ -116,6 +116,17 @@ amb_status sir_batch_step(SirBatch &sb, cudaStream_t s, uint64_t *launches);
 void sir_batch_finish(SirBatch &sb, amb_pop **pops, const uint32_t *steps, uint32_t n);
 void sir_batch_release(SirBatch &sb, cudaStream_t s);
 
+amb_status check_params(amb_model model, const amb_params *p, uint64_t seed);
+
+// Advance pops[i] by ks[i] steps with the batched launches (optionally as one
+// CUDA graph); *launches += kernels launched, *ms = device time.
+amb_status advance(const std::vector<amb_pop *> &pops, const std::vector<uint32_t> &ks, BandShape shape,
+                   cudaStream_t s, bool graph, uint64_t *launches, float *ms);
+// Device error words of the populations (one synchronisation), and the first
+// one as a status.
+amb_status read_errors(const std::vector<amb_pop *> &pops, cudaStream_t s, std::vector<uint32_t> &words);
+amb_status check_errors(const std::vector<amb_pop *> &pops, cudaStream_t s);
+
 // Step-count rows of a population: capacity for `rows` steps.
 amb_status ensure_series(amb_pop *pop, uint64_t rows);
 

@@ -28,6 +28,133 @@ struct amb_batch {
     double ms = 0.0;
 };
 
+namespace amb {
+
+// Advance every population by its own number of steps (ks[i] for pops[i]):
+// one shared band launch per SIR step over all SIR populations, one launch for
+// all small wealth populations (all their steps), three shared launches per
+// step for the large ones, one launch per walk population.  With graph, the
+// launches are captured into one CUDA graph and launched once.  *ms: device
+// time of the launches (events on s).  Returns after the work is done.
+amb_status advance(const std::vector<amb_pop *> &pops, const std::vector<uint32_t> &ks, BandShape shape,
+                   cudaStream_t s, bool graph, uint64_t *launches_out, float *ms_out)
+{
+    std::vector<amb_pop *> sir, wealth, walk;
+    std::vector<uint32_t> sir_steps, wealth_steps, walk_steps_v;
+    uint32_t max_large = 0, max_sir = 0;
+    for (size_t i = 0; i < pops.size(); ++i) {
+        amb_pop *p = pops[i];
+        const uint32_t k = ks[i];
+        if (p->t + k >= (uint64_t)kInitStep) return fail(AMB_EINVAL, "job %zu: too many steps", i);
+        AMB_TRY(ensure_series(p, p->t + k));
+        if (k) AMB_TRY_CUDA(cudaMemsetAsync(p->series + (size_t)p->t * 4u, 0, (size_t)k * 4u * sizeof(int64_t), s));
+        if (p->model == AMB_SIR) {
+            sir.push_back(p);
+            sir_steps.push_back(k);
+            max_sir = std::max(max_sir, k);
+        } else if (p->model == AMB_WEALTH) {
+            wealth.push_back(p);
+            wealth_steps.push_back(k);
+            if (!wealth_uses_smem(p->p.n) && p->p.n) max_large = std::max(max_large, k);
+        } else {
+            walk.push_back(p);
+            walk_steps_v.push_back(k);
+        }
+    }
+    SirBatch sb;
+    WealthBatch wb;
+    amb_status r = sir_batch_build(sb, sir.data(), sir_steps.data(), (uint32_t)sir.size(), shape, s);
+    if (r == AMB_OK) r = wealth_batch_build(wb, wealth.data(), wealth_steps.data(), (uint32_t)wealth.size(), s);
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    uint64_t launches = 0;
+    if (r == AMB_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        r = fail(AMB_ECUDA, "event creation failed");
+    auto issue = [&]() -> amb_status {
+        AMB_TRY(wealth_batch_small(wb, s, &launches));
+        for (size_t q = 0; q < walk.size(); ++q) {
+            if (walk_steps_v[q] == 0) continue;
+            AMB_TRY(walk_steps(walk[q], walk_steps_v[q]));
+            launches += 1;
+        }
+        const uint32_t steps = std::max(max_sir, max_large);
+        for (uint32_t k = 0; k < steps; ++k) {
+            if (k < max_sir) AMB_TRY(sir_batch_step(sb, s, &launches));
+            if (k < max_large) AMB_TRY(wealth_batch_large_step(wb, s, &launches));
+        }
+        return AMB_OK;
+    };
+    if (r == AMB_OK && graph) {
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            r = fail(AMB_ECUDA, "stream capture failed to begin (is the stream the legacy default stream?)");
+        } else {
+            r = issue();
+            const cudaError_t ec = cudaStreamEndCapture(s, &g);
+            if (r == AMB_OK && ec != cudaSuccess) r = fail(AMB_ECUDA, "capture: %s", cudaGetErrorString(ec));
+            if (r == AMB_OK && cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) r = fail(AMB_ECUDA, "graph instantiate failed");
+        }
+        if (r == AMB_OK) {
+            cudaEventRecord(e0, s);
+            if (cudaGraphLaunch(ge, s) != cudaSuccess) r = fail(AMB_ECUDA, "graph launch failed");
+            cudaEventRecord(e1, s);
+        }
+    } else if (r == AMB_OK) {
+        cudaEventRecord(e0, s);
+        r = issue();
+        cudaEventRecord(e1, s);
+    }
+    if (r == AMB_OK) {
+        const cudaError_t es = cudaEventSynchronize(e1);
+        if (es != cudaSuccess) r = fail(AMB_ECUDA, "batched steps: %s", cudaGetErrorString(es));
+        float ms = 0.f;
+        if (r == AMB_OK) cudaEventElapsedTime(&ms, e0, e1);
+        if (ms_out) *ms_out = ms;
+        sir_batch_finish(sb, sir.data(), sir_steps.data(), (uint32_t)sir.size());
+        for (size_t q = 0; q < wealth.size(); ++q) {
+            wealth[q]->t += wealth_steps[q];
+            wealth[q]->launches += wealth_steps[q];
+        }
+        for (size_t q = 0; q < walk.size(); ++q) {
+            walk[q]->t += walk_steps_v[q];
+            walk[q]->index_valid = false;
+        }
+        if (launches_out) *launches_out += launches;
+    }
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    sir_batch_release(sb, s);
+    wealth_batch_release(wb, s);
+    cudaStreamSynchronize(s);
+    return r;
+}
+
+// The error words of every population (one synchronisation).
+amb_status read_errors(const std::vector<amb_pop *> &pops, cudaStream_t s, std::vector<uint32_t> &words)
+{
+    words.assign(pops.size(), 0u);
+    for (size_t i = 0; i < pops.size(); ++i)
+        AMB_TRY_CUDA(cudaMemcpyAsync(&words[i], pops[i]->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    AMB_TRY_CUDA(cudaStreamSynchronize(s));
+    return AMB_OK;
+}
+
+amb_status check_errors(const std::vector<amb_pop *> &pops, cudaStream_t s)
+{
+    std::vector<uint32_t> h;
+    AMB_TRY(read_errors(pops, s, h));
+    for (size_t i = 0; i < pops.size(); ++i) {
+        if (h[i] & ERR_TIMEOUT) return fail(AMB_ETIMEOUT, "job %zu: a bounded device-side wait ran out (0x%x)", i, h[i]);
+        if (h[i]) return fail(AMB_EINVARIANT, "job %zu: device reported an out-of-range value (0x%x)", i, h[i]);
+    }
+    return AMB_OK;
+}
+
+}  // namespace amb
+
+
 namespace {
 
 void destroy_pops(std::vector<amb_pop *> &pops)
@@ -48,20 +175,6 @@ amb_status create_pops(const amb_job *jobs, size_t n, cudaStream_t s, std::vecto
             destroy_pops(pops);
             return st;
         }
-    }
-    return AMB_OK;
-}
-
-// The error words of every population, read with one synchronisation.
-amb_status check_errors(const std::vector<amb_pop *> &pops, cudaStream_t s)
-{
-    std::vector<uint32_t> h(pops.size(), 0u);
-    for (size_t i = 0; i < pops.size(); ++i)
-        AMB_TRY_CUDA(cudaMemcpyAsync(&h[i], pops[i]->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    AMB_TRY_CUDA(cudaStreamSynchronize(s));
-    for (size_t i = 0; i < pops.size(); ++i) {
-        if (h[i] & ERR_TIMEOUT) return fail(AMB_ETIMEOUT, "job %zu: a bounded device-side wait ran out (0x%x)", i, h[i]);
-        if (h[i]) return fail(AMB_EINVARIANT, "job %zu: device reported an out-of-range value (0x%x)", i, h[i]);
     }
     return AMB_OK;
 }
@@ -162,98 +275,16 @@ amb_status amb_batch_run(amb_batch *b, const amb_tune *tune, double *ms_out)
     const bool graph = !tune || tune->use_graph;
     if (tune && tune->autotune) AMB_TRY(autotune_shape(b->jobs, s, &shape));
     b->shape = shape;
-    std::vector<amb_pop *> sir, wealth, walk;
-    std::vector<uint32_t> sir_steps, wealth_steps, walk_steps_v;
-    uint32_t max_large = 0, max_sir = 0;
-    for (size_t i = 0; i < b->pops.size(); ++i) {
-        amb_pop *p = b->pops[i];
-        const uint32_t k = b->jobs[i].steps;
-        if (p->t + k >= (uint64_t)kInitStep) return fail(AMB_EINVAL, "job %zu: too many steps", i);
-        AMB_TRY(ensure_series(p, p->t + k));
-        if (k) AMB_TRY_CUDA(cudaMemsetAsync(p->series + (size_t)p->t * 4u, 0, (size_t)k * 4u * sizeof(int64_t), s));
-        if (p->model == AMB_SIR) {
-            sir.push_back(p);
-            sir_steps.push_back(k);
-            max_sir = std::max(max_sir, k);
-        } else if (p->model == AMB_WEALTH) {
-            wealth.push_back(p);
-            wealth_steps.push_back(k);
-            if (!wealth_uses_smem(p->p.n) && p->p.n) max_large = std::max(max_large, k);
-        } else {
-            walk.push_back(p);
-            walk_steps_v.push_back(k);
-        }
-    }
-    SirBatch sb;
-    WealthBatch wb;
-    amb_status r = sir_batch_build(sb, sir.data(), sir_steps.data(), (uint32_t)sir.size(), shape, s);
-    if (r == AMB_OK) r = wealth_batch_build(wb, wealth.data(), wealth_steps.data(), (uint32_t)wealth.size(), s);
-    cudaGraph_t g = nullptr;
-    cudaGraphExec_t ge = nullptr;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    std::vector<uint32_t> ks(b->jobs.size());
+    for (size_t i = 0; i < ks.size(); ++i) ks[i] = b->jobs[i].steps;
     uint64_t launches = 0;
-    if (r == AMB_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
-        r = fail(AMB_ECUDA, "event creation failed");
-    auto issue = [&]() -> amb_status {
-        AMB_TRY(wealth_batch_small(wb, s, &launches));
-        for (size_t q = 0; q < walk.size(); ++q) {
-            AMB_TRY(walk_steps(walk[q], walk_steps_v[q]));
-            launches += 1;
-        }
-        const uint32_t steps = std::max(max_sir, max_large);
-        for (uint32_t k = 0; k < steps; ++k) {
-            if (k < max_sir) AMB_TRY(sir_batch_step(sb, s, &launches));
-            if (k < max_large) AMB_TRY(wealth_batch_large_step(wb, s, &launches));
-        }
-        return AMB_OK;
-    };
-    if (r == AMB_OK && graph) {
-        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-            r = fail(AMB_ECUDA, "stream capture failed to begin (is the stream the legacy default stream?)");
-        } else {
-            r = issue();
-            const cudaError_t ec = cudaStreamEndCapture(s, &g);
-            if (r == AMB_OK && ec != cudaSuccess) r = fail(AMB_ECUDA, "capture: %s", cudaGetErrorString(ec));
-            if (r == AMB_OK && cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) r = fail(AMB_ECUDA, "graph instantiate failed");
-        }
-        if (r == AMB_OK) {
-            cudaEventRecord(e0, s);
-            if (cudaGraphLaunch(ge, s) != cudaSuccess) r = fail(AMB_ECUDA, "graph launch failed");
-            cudaEventRecord(e1, s);
-        }
-    } else if (r == AMB_OK) {
-        cudaEventRecord(e0, s);
-        r = issue();
-        cudaEventRecord(e1, s);
-    }
-    if (r == AMB_OK) {
-        const cudaError_t es = cudaEventSynchronize(e1);
-        if (es != cudaSuccess) r = fail(AMB_ECUDA, "batch run: %s", cudaGetErrorString(es));
-        float ms = 0.f;
-        if (r == AMB_OK) cudaEventElapsedTime(&ms, e0, e1);
-        b->ms = ms;
-        if (ms_out) *ms_out = ms;
-        sir_batch_finish(sb, sir.data(), sir_steps.data(), (uint32_t)sir.size());
-        for (size_t q = 0; q < wealth.size(); ++q) {
-            wealth[q]->t += wealth_steps[q];
-            wealth[q]->launches += wealth_steps[q];
-        }
-        for (size_t q = 0; q < walk.size(); ++q) {
-            walk[q]->t += walk_steps_v[q];
-            walk[q]->index_valid = false;
-        }
-        b->launches = launches;
-        b->ran = true;
-    }
-    if (ge) cudaGraphExecDestroy(ge);
-    if (g) cudaGraphDestroy(g);
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    sir_batch_release(sb, s);
-    wealth_batch_release(wb, s);
-    cudaStreamSynchronize(s);
-    if (r == AMB_OK) r = check_errors(b->pops, s);
-    return r;
+    float ms = 0.f;
+    AMB_TRY(advance(b->pops, ks, shape, s, graph, &launches, &ms));
+    b->ms = ms;
+    if (ms_out) *ms_out = ms;
+    b->launches = launches;
+    b->ran = true;
+    return check_errors(b->pops, s);
 }
 
 amb_status amb_batch_population(amb_batch *b, size_t i, amb_pop **pop)

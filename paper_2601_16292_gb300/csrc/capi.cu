@@ -254,11 +254,13 @@ amb_status amb_sir_thresholds(double beta, double gamma, uint32_t cap, uint32_t 
     return host_thresholds(beta, gamma, cap, t_inf, K, t_rec);
 }
 
-amb_status amb_create(amb_model model, const amb_params *p, uint64_t seed, uint32_t replicate, void *cuda_stream,
-                      amb_pop **out)
+}  // extern "C"
+
+namespace amb {
+// The checks amb_create makes on its arguments (no GPU call).
+amb_status check_params(amb_model model, const amb_params *p, uint64_t seed)
 {
-    if (!p || !out) return fail(AMB_EINVAL, "null pointer");
-    *out = nullptr;
+    if (!p) return fail(AMB_EINVAL, "null pointer");
     if (model != AMB_WEALTH && model != AMB_WALK && model != AMB_SIR) return fail(AMB_EINVAL, "unknown model %d", (int)model);
     if (seed > 0xFFFFFFFFull) return fail(AMB_EINVAL, "seed must be < 2^32");
     if (p->n > 0x7FFFFFFFu) return fail(AMB_EINVAL, "n must be < 2^31");
@@ -273,6 +275,19 @@ amb_status amb_create(amb_model model, const amb_params *p, uint64_t seed, uint3
         if (p->n_init_infected > p->n) return fail(AMB_EINVAL, "n_init_infected > n");
         if (p->variant > AMB_SIR_BAND) return fail(AMB_EINVAL, "unknown SIR variant %u", p->variant);
     }
+    return AMB_OK;
+}
+}  // namespace amb
+
+extern "C" {
+
+amb_status amb_create(amb_model model, const amb_params *p, uint64_t seed, uint32_t replicate, void *cuda_stream,
+                      amb_pop **out)
+{
+    if (!p || !out) return fail(AMB_EINVAL, "null pointer");
+    *out = nullptr;
+    AMB_TRY(check_params(model, p, seed));
+    const uint32_t L = p->grid_side;
     amb_pop *pop = new (std::nothrow) amb_pop();
     if (!pop) return fail(AMB_ENOMEM, "host allocation failed");
     pop->model = model;

@@ -873,9 +873,6 @@ amb_status sir_band_init(amb_pop *pop, const int32_t *x, const int32_t *y, const
         if (!pop->row_start[b]) AMB_TRY(dalloc(&pop->row_start[b], (size_t)L + 1, s));
     }
     if (!pop->start) AMB_TRY(dalloc(&pop->start, C + 1, s));
-    // 32-bit per-CTA counters for bands whose source rows hold >= 65536 agents
-    if (n >= kPackedLimit && !pop->band_wide)
-        AMB_TRY(dalloc(&pop->band_wide, (size_t)pop->band_grid * 2u * H * L, s));
     int32_t *cnt = nullptr, *cursor = nullptr;
     AMB_TRY(dalloc(&cnt, C, s));
     AMB_TRY(dalloc(&cursor, C, s));
@@ -918,6 +915,10 @@ amb_status sir_band_steps(amb_pop *pop, uint32_t k)
     const size_t smem = pop->band_smem;
     AMB_TRY_CUDA(cudaFuncSetAttribute(sir_band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     AMB_TRY(pop->lb.ensure(pop->n_bands, s));
+    // 32-bit per-CTA counters for bands whose source rows hold >= 65536 agents
+    // (allocated on the first step that may need them; batched steps use their own)
+    if (pop->p.n >= kPackedLimit && !pop->band_wide)
+        AMB_TRY(dalloc(&pop->band_wide, (size_t)pop->band_grid * 2u * pop->band_rows * pop->p.grid_side, s));
     BandArgs a;
     round_keys(pop->key0, pop->key1, a.rk0, a.rk1);
     for (uint32_t j = 0; j < k; ++j) {
@@ -1003,9 +1004,9 @@ static amb_status sir_band_regeometry(amb_pop *pop, BandShape shape)
     pop->n_bands = g.n_bands;
     pop->band_grid = std::min<uint32_t>(g.n_bands, grid_max);
     pop->band_smem = g.smem;
-    if (pop->p.n >= kPackedLimit && grow) {
+    if (pop->band_wide && grow) {  // re-sized on the next single-population step
         dfree(pop->band_wide, s);
-        AMB_TRY(dalloc(&pop->band_wide, (size_t)pop->band_grid * 2u * g.H * L, s));
+        pop->band_wide = nullptr;
     }
     AMB_TRY(pop->lb.ensure(pop->n_bands, s));
     return AMB_OK;

@@ -95,3 +95,33 @@ def test_binding_structs_match_header_layout(tmp_path):
         assert c[name] == ctypes.sizeof(cls), name
         for f, _ in cls._fields_:
             assert c["%s.%s" % (name, f)] == getattr(cls, f).offset, (name, f)
+
+
+def test_job_bytes_host_only():
+    job = amb.make_job("sir", 100_000, seed=1, steps=100, L=408, beta=0.1, gamma=0.02, n0=100)
+    r, t = amb.amb_job_bytes(job)
+    C = 408 * 408
+    # records, cell index and thresholds at least; creation scratch: columns + counters
+    assert r >= 16 * 100_000 + 4 * C + 4 * 100_000
+    assert t == 9 * 100_000 + 8 * C
+    r2, _ = amb.amb_job_bytes(amb.make_job("sir", 200_000, seed=1, steps=100, L=408, beta=0.1, gamma=0.02, n0=100))
+    assert r2 > r
+    rw, tw = amb.amb_job_bytes(amb.make_job("walk", 100_000, seed=1, steps=100, L=408))
+    assert tw == 0 and 8 * 100_000 <= rw < r
+    small, _ = amb.amb_job_bytes(amb.make_job("wealth", 1000, seed=1, steps=100))
+    large, _ = amb.amb_job_bytes(amb.make_job("wealth", 100_000, seed=1, steps=100))
+    assert large - small >= 8 * 99_000  # large wealth populations keep a credit column
+    # the per-step count rows grow with the steps
+    a, _ = amb.amb_job_bytes(amb.make_job("walk", 1000, seed=1, steps=10, L=40))
+    b, _ = amb.amb_job_bytes(amb.make_job("walk", 1000, seed=1, steps=10_000, L=40))
+    assert b - a >= 32 * (10_000 - 64)
+
+
+def test_job_bytes_rejects_what_create_rejects():
+    with pytest.raises(amb.AmbError) as e:
+        amb.amb_job_bytes(amb.make_job("sir", 10, seed=1, steps=1, L=4, beta=1.5, gamma=0.1, n0=1))
+    assert e.value.status == amb.AMB_EINVAL
+    with pytest.raises(amb.AmbError):
+        amb.amb_job_bytes(amb.make_job("sir", 10, seed=1, steps=1, L=4, beta=0.5, gamma=0.1, n0=11))
+    with pytest.raises(amb.AmbError):
+        amb.amb_job_bytes(amb.make_job("walk", 10, seed=1 << 33, steps=1, L=4))
