@@ -276,6 +276,82 @@ def sweep_bench(amb, torch, stream, rank, world):
             "speedup_device": dev_ms / ms, "unit": "agent-steps/s"}
 
 
+def _latency_summary(lat, total, span):
+    import numpy as np
+    lat = np.asarray(lat)
+    return {"value": total / span, "makespan_s": span, "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()), "max_s": float(lat.max())}
+
+
+def serve_bench(amb, torch, stream, rank, world, n_jobs=5000, chunk=32, budget_gb=120):
+    """The serving trace (5,000 jobs, Poisson arrivals at 200/s; ranks split the
+    trace) replayed in real time: served by the continuous-batching loop under a
+    120 GB budget, and by one-at-a-time stepping through the plain API (each job
+    created, stepped, its counts read, destroyed; a job starts when it has
+    arrived and the previous one is done).  Latency = arrival to result read."""
+    from paper_2601_16292_gb300 import workloads
+    arrivals, jobs = workloads.serve_trace(n_jobs=n_jobs)
+    arrivals, jobs = arrivals[rank::world], jobs[rank::world]
+    total = workloads.agent_steps(jobs)
+    srv = amb.Server(int(budget_gb * 1e9), stream, chunk_steps=chunk)
+    # warm the worker's code paths on a few throwaway jobs
+    for j in workloads.scaled(jobs[:6], 20_000):
+        srv.submit(j)
+    srv.drain(120.0)
+    base = srv.stats()
+    tickets = []
+    t0 = time.perf_counter()
+    for a, j in zip(arrivals, jobs):
+        d = a - (time.perf_counter() - t0)
+        if d > 0:
+            time.sleep(d)
+        tickets.append(srv.submit(j))
+    srv.drain(3600.0)
+    res = [srv.poll(t) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    first = min(r["submit_s"] for r in res)
+    served = _latency_summary([r["done_s"] - r["submit_s"] for r in res], total,
+                              max(r["done_s"] for r in res) - first)
+    served.update({"iterations": st["iterations"] - base["iterations"], "launches": st["launches"] - base["launches"],
+                   "hbm_peak_gb": st["hbm_peak"] / 1e9, "chunk_steps": chunk,
+                   "failed": st["failed"] - base["failed"], "busy_s": st["busy_s"] - base["busy_s"]})
+    # one job at a time on the same trace
+    def one_at_a_time(arr):
+        lat = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for a, j in zip(arr, jobs):
+            d = a - (time.perf_counter() - t0)
+            if d > 0:
+                time.sleep(d)
+            kw = {k: v for k, v in j.items() if k not in ("model", "steps")}
+            p = amb.Population(j["model"], stream=stream, **kw)
+            amb.amb_step(p.handle, j["steps"])
+            p.counts()
+            p.close()
+            lat.append(time.perf_counter() - t0 - a)
+        return _latency_summary(lat, total, time.perf_counter() - t0 - arr[0])
+
+    one = one_at_a_time(arrivals)
+    # capacity: every job queued at t = 0
+    srv = amb.Server(int(budget_gb * 1e9), stream, chunk_steps=chunk)
+    t0 = time.perf_counter()
+    tickets = [srv.submit(j) for j in jobs]
+    srv.drain(3600.0)
+    res = [srv.poll(t) for t in tickets]
+    srv.close()
+    sat_served = _latency_summary([r["done_s"] - r["submit_s"] for r in res], total,
+                                  max(r["done_s"] for r in res) - min(r["submit_s"] for r in res))
+    sat_one = one_at_a_time([0.0] * len(jobs))
+    return {"jobs": len(jobs), "agent_steps": total, "arrival_rate_per_s": 200.0 / world,
+            "budget_gb": budget_gb, "offered_load": total / float(arrivals[-1] - arrivals[0]),
+            "trace": {"served": served, "one_at_a_time": one},
+            "saturated": {"served": sat_served, "one_at_a_time": sat_one,
+                          "speedup_throughput": sat_served["value"] / sat_one["value"]},
+            "unit": "agent-steps/s"}
+
+
 def cpu_baseline(budget_s=15.0):
     """The oracle as it stands on one host core: the full 10M-agent SIR
     population, as many whole steps as fit in the budget (at least one)."""
@@ -321,6 +397,7 @@ def gpu_arm(args):
     agent_steps = sum_over_ranks(world, float(SIR_CFG["n"]) * args.steps, device)
     e2e = None if only_sir else run_e2e(amb, torch, max(args.steps, 3), rank, stream)
     e2e_val = None if only_sir else sum_over_ranks(world, e2e["value"], device)
+    serve = None if only_sir else serve_bench(amb, torch, stream, rank, world)
 
     if rank != 0:
         if world > 1:
@@ -370,6 +447,7 @@ def gpu_arm(args):
         "invariants_ok": bool(inv["ok"]),
         "models": {"wealth_10k_100steps": wealth, "walk_1M_L1000_200steps": walk},
         "sweep_1024_jobs": sweep,
+        "serve_5000_jobs": serve,
     }
     print(json.dumps(line))
     if world > 1:
@@ -424,8 +502,10 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="amb", choices=["amb", "reference"])
-    ap.add_argument("--only", default="all", choices=["all", "sir", "sweep"],
-                    help="sir: time the SIR step alone (no extras; for profiling); sweep: the sweep alone")
+    ap.add_argument("--only", default="all", choices=["all", "sir", "sweep", "serve"],
+                    help="sir: time the SIR step alone (no extras; for profiling); sweep / serve: that part alone")
+    ap.add_argument("--serve-jobs", type=int, default=5000)
+    ap.add_argument("--serve-chunk", type=int, default=32)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -434,6 +514,13 @@ def main():
         from paper_2601_16292_gb300 import amb
         torch.cuda.set_device(0)
         print(json.dumps(sweep_bench(amb, torch, torch.cuda.Stream(), 0, 1)))
+        return
+    if args.impl == "amb" and args.only == "serve":
+        import torch
+        from paper_2601_16292_gb300 import amb
+        torch.cuda.set_device(0)
+        print(json.dumps(serve_bench(amb, torch, torch.cuda.Stream(), 0, 1, n_jobs=args.serve_jobs,
+                                     chunk=args.serve_chunk)))
         return
     if args.impl == "reference":
         reference_arm(args)

@@ -299,8 +299,10 @@ typedef struct {
                                 transient of the job being admitted) */
     uint32_t max_active;     /* jobs on the device at once; 0 = 4096 */
     uint32_t chunk_steps;    /* steps per job per iteration; 0 = 32 */
-    uint32_t band_rows_cap;  /* SIR band shape (as in amb_tune); 0 = 16 */
-    int32_t spread_bands;
+    uint32_t band_rows_cap;  /* SIR band height cap (as in amb_tune); 0 = 16 */
+    int32_t spread_bands;    /* 0: per iteration, spread the bands over every SM when
+                                the active SIR jobs' fewest bands would leave SMs idle;
+                                1: always spread; -1: always the fewest bands */
 } amb_server_config;
 
 typedef struct {

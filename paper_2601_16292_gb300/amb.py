@@ -365,10 +365,10 @@ def _result_dict(r):
             "last": list(r.last), "submit_s": r.submit_s, "admit_s": r.admit_s, "done_s": r.done_s}
 
 
-def amb_server_create(hbm_budget_bytes, stream, max_active=0, chunk_steps=0, band_rows_cap=0, spread_bands=False):
+def amb_server_create(hbm_budget_bytes, stream, max_active=0, chunk_steps=0, band_rows_cap=0, spread_bands=0):
     cfg = amb_server_config(hbm_budget_bytes=int(hbm_budget_bytes), max_active=int(max_active),
                             chunk_steps=int(chunk_steps), band_rows_cap=int(band_rows_cap),
-                            spread_bands=int(bool(spread_bands)))
+                            spread_bands=int(spread_bands))
     h = ctypes.c_void_p()
     _check(lib().amb_server_create(ctypes.byref(cfg), _stream_handle(stream), ctypes.byref(h)))
     return h

@@ -108,6 +108,9 @@ struct SirBatch {
 struct BandShape {
     uint32_t rows_cap = 32;
     bool spread = false;
+    // adaptive: spread when the fewest bands of all live populations would
+    // not give every SM two bands, else fewest
+    bool adaptive = false;
 };
 amb_status sir_batch_build(SirBatch &sb, amb_pop **pops, const uint32_t *steps, uint32_t n, BandShape shape,
                            cudaStream_t s);

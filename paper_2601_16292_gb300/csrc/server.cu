@@ -156,7 +156,8 @@ void worker_loop(amb_server *S)
     const uint32_t chunk = S->cfg.chunk_steps ? S->cfg.chunk_steps : 32u;
     BandShape shape;
     shape.rows_cap = S->cfg.band_rows_cap ? std::min<uint32_t>(S->cfg.band_rows_cap, 32u) : 16u;
-    shape.spread = S->cfg.spread_bands != 0;
+    shape.spread = S->cfg.spread_bands > 0;
+    shape.adaptive = S->cfg.spread_bands == 0;
     for (;;) {
         std::vector<ServerJob *> admit;
         {

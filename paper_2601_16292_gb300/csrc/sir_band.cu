@@ -1022,6 +1022,15 @@ amb_status sir_batch_build(SirBatch &sb, amb_pop **pops, const uint32_t *steps, 
     size_t smem = 16, wide_words = 0;
     for (uint32_t q = 0; q < n; ++q) base = std::max<uint32_t>(base, pops[q]->lb.launches);
     sb.epoch_base = base;  // batch epochs continue after every population's own
+    if (shape.adaptive) {
+        uint64_t fewest = 0;
+        for (uint32_t q = 0; q < n; ++q) {
+            BandGeometry g;
+            if (steps[q] && pops[q]->p.n && band_geometry(pops[q]->p.grid_side, grid_max, &g, shape.rows_cap, false))
+                fewest += g.n_bands;
+        }
+        shape.spread = fewest < 2ull * grid_max;
+    }
     AMB_TRY(dalloc(&sb.d_codes, (size_t)std::max<uint32_t>(n, 1u) * 512u, s));
     for (uint32_t q = 0; q < n; ++q) {
         amb_pop *p = pops[q];
