@@ -48,6 +48,22 @@ def sir_bytes_per_agent_step(n, L, path):
     return 18.0 + 8.0 + 8.0 * C / n
 
 
+def profiled_traffic(key):
+    """DRAM bytes (read + write) per launch of the kernel from the committed ncu
+    capture, or None when the kernel's sources changed since the capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)[key]
+        h = hashlib.sha1()
+        for p in d["source_files"]:
+            with open(os.path.join(ROOT, p), "rb") as f:
+                h.update(f.read())
+        return d["dram_bytes_per_launch"] if h.hexdigest() == d["source_sha1"] else None
+    except Exception:
+        return None
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -411,12 +427,7 @@ def gpu_arm(args):
     step_ms = per_sorted[len(per_sorted) // 2]
     achieved = b_alg * n / (step_ms / 1e3) / 1e9
     value = agent_steps / (total_ms_max / 1e3)
-    traffic = None
-    try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            traffic = json.load(f).get("sir_%s" % path)
-    except Exception:
-        traffic = None
+    traffic = profiled_traffic("sir_%s" % path)
     line = {
         "metric": "agent-steps/s (spatial SIR, 10M agents, 4096x4096 torus)",
         "value": value,
