@@ -128,15 +128,23 @@ class ClockSampler:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def dist_setup(n_gpus):
+def dist_setup(n_gpus, backend="nccl"):
+    """(world, rank, local rank) from the torchrun environment; joins the
+    process group when there is more than one rank (only barriers and the
+    final max / sum of scalars use it: ranks never exchange data)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        dist.init_process_group("nccl")
+        dist.init_process_group(backend)
     return world, rank, local
+
+
+def partition(items, rank, world):
+    """This rank's share of a job list (round robin; every item exactly once)."""
+    return items[rank::world]
 
 
 def barrier(world):
@@ -257,7 +265,7 @@ def sweep_bench(amb, torch, stream, rank, world):
     ranks split the job list): one batch, graph-captured and autotuned, against
     the same jobs stepped one at a time through amb_step on the same GPU."""
     from paper_2601_16292_gb300 import workloads
-    jobs = workloads.sweep_jobs()[rank::world]
+    jobs = partition(workloads.sweep_jobs(), rank, world)
     total = workloads.agent_steps(jobs)
     b = amb.Batch(jobs, stream=stream)
     torch.cuda.synchronize()
@@ -307,7 +315,7 @@ def serve_bench(amb, torch, stream, rank, world, n_jobs=5000, chunk=32, budget_g
     arrived and the previous one is done).  Latency = arrival to result read."""
     from paper_2601_16292_gb300 import workloads
     arrivals, jobs = workloads.serve_trace(n_jobs=n_jobs)
-    arrivals, jobs = arrivals[rank::world], jobs[rank::world]
+    arrivals, jobs = partition(arrivals, rank, world), partition(jobs, rank, world)
     total = workloads.agent_steps(jobs)
     srv = amb.Server(int(budget_gb * 1e9), stream, chunk_steps=chunk)
     # warm the worker's code paths on a few throwaway jobs
