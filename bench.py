@@ -33,19 +33,19 @@ WALK_CFG = dict(n=1_000_000, L=1000, seed=1, steps=200)
 L2_BYTES = 129 * 1024 * 1024
 
 
-def sir_bytes_per_agent_step(n, L, path):
-    """Algorithmic HBM bytes of one SIR step per agent for the layout in use.
-
-    band path (cell-ordered records): read + write one 8-byte record per
-    agent (id + packed x/state/next draws), write start[C] once -> 16 + 4 C/N.
-    generic path (id-ordered columns): read/write x, y (16), read state (1) and
-    write it (1), cell-id write + read of cnt/inf/cursor/start/ids per agent and
-    per cell: counted as 18 + 8 (ids write/read) + 8 C / N.
-    """
+def sir_bytes_per_agent_step(n, L):
+    """Algorithmic HBM bytes of one SIR step per agent (the method's own count,
+    independent of the layout): read and write x, y (int32) and state (uint8)
+    = 18 B, the cell-order permutation written and read = 8 B, the cell index
+    start[C] written and read = 8 C / N B.  39.42 B at 10M agents on 4096^2."""
     C = L * L
-    if path == "band":
-        return 16.0 + 4.0 * C / n
     return 18.0 + 8.0 + 8.0 * C / n
+
+
+def sir_layout_bytes_per_agent_step(n, L):
+    """Compulsory traffic of this build's layout: one 8-byte cell-ordered
+    record read and written per agent, start[C] written once: 16 + 4 C / N."""
+    return 16.0 + 4.0 * L * L / n
 
 
 def profiled_traffic(key):
@@ -430,7 +430,8 @@ def gpu_arm(args):
         return
     hbm, peak_kind = load_peaks()
     n, L = SIR_CFG["n"], SIR_CFG["L"]
-    b_alg = sir_bytes_per_agent_step(n, L, path)
+    b_alg = sir_bytes_per_agent_step(n, L)
+    b_layout = sir_layout_bytes_per_agent_step(n, L)
     per_sorted = sorted(per)
     step_ms = per_sorted[len(per_sorted) // 2]
     achieved = b_alg * n / (step_ms / 1e3) / 1e9
@@ -453,9 +454,10 @@ def gpu_arm(args):
                    "gamma": SIR_CFG["gamma"], "n_init_infected": SIR_CFG["n0"], "seed": SIR_CFG["seed"],
                    "sir_path": path, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "working set %.0f MB > L2 129 MB (no flush needed)" % (
-                       (b_alg * n) / 1e6)},
+                       (b_layout * n) / 1e6)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "peak_kind": peak_kind, "traffic": traffic, "bytes_per_agent_step": b_alg,
+                     "layout_bytes_per_agent_step": b_layout, "layout_frac": b_layout * n / (step_ms / 1e3) / 1e9 / hbm,
                      "kernel_ms_median": step_ms},
         "cpu_baseline": None if only_sir else cpu_baseline(),
         "e2e": None if only_sir else {"value": e2e_val, "unit": "agent-steps/s",
