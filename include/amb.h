@@ -280,8 +280,8 @@ amb_status amb_batch_destroy(amb_batch *b);
 /* Device memory one job needs (host-only arithmetic, no GPU call):
  * *resident = what its population holds while it exists (columns or
  * cell-ordered records, cell index, thresholds, count rows, look-back words),
- * *transient = what its creation holds on top for a moment (initial columns and
- * counting-sort scratch).  Stream-ordered pool rounding is not included. */
+ * *transient = what its creation holds on top for a moment (initial columns,
+ * the cell-ordered id list and counting-sort scratch).  Stream-ordered pool rounding is not included. */
 amb_status amb_job_bytes(const amb_job *job, size_t *resident, size_t *transient);
 
 /* ------------------------------------------------------------ serving ----

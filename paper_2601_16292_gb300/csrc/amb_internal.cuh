@@ -189,8 +189,7 @@ struct amb_pop {
     bool index_valid = false;
 
     // SIR band path: cell-ordered records, double-buffered
-    uint32_t *rec_id[2] = {nullptr, nullptr};
-    uint32_t *rec_aux[2] = {nullptr, nullptr};
+    uint2 *rec[2] = {nullptr, nullptr};  // {id, word} per slot
     int32_t *row_start[2] = {nullptr, nullptr};
     int cur = 0;
     uint32_t band_rows = 0, n_bands = 0;

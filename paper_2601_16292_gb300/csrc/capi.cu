@@ -551,7 +551,15 @@ amb_status amb_read_index(amb_pop *pop, int32_t *start, int32_t *ids, int dst_on
     AMB_TRY(device_error(pop));
     if (uses_band(pop)) {
         AMB_TRY(copy_out(pop->start, start, (C + 1) * sizeof(int32_t), dst_on_device, pop->stream));
-        return copy_out(pop->rec_id[pop->cur], ids, (size_t)pop->p.n * sizeof(int32_t), dst_on_device, pop->stream);
+        // the id list is the id half of the cell-ordered records
+        const size_t n = pop->p.n;
+        if (n == 0) return AMB_OK;
+        int32_t *tmp = nullptr;
+        AMB_TRY(dalloc(&tmp, n, pop->stream));
+        amb_status st = sir_band_read(pop, (amb_col)-1, tmp);
+        if (st == AMB_OK) st = copy_out(tmp, ids, n * sizeof(int32_t), dst_on_device, pop->stream);
+        dfree(tmp, pop->stream);
+        return st;
     }
     if (!pop->index_valid) AMB_TRY(build_index(pop));
     AMB_TRY(copy_out(pop->start, start, (C + 1) * sizeof(int32_t), dst_on_device, pop->stream));

@@ -95,8 +95,9 @@ extern "C" amb_status amb_job_bytes(const amb_job *job, size_t *resident, size_t
         // look-back words of the cell-index scan and of the bands
         const uint64_t tiles = std::max<uint64_t>(scan_tiles((uint32_t)C), L);
         r += 16 * (n + 4) + 8 * (L + 1) + 4 * (C + 1) + 4 * (n + 2) + 8 * std::max<uint64_t>(tiles, 1024) + 16;
-        // initial columns (x, y, state) and the counting sort's counters
-        t = 9 * n + 8 * C;
+        // initial columns (x, y, state), the cell-ordered id list and the
+        // counting sort's counters
+        t = 13 * n + 8 * C;
         break;
     }
     }

@@ -1,8 +1,9 @@
 // sir_band.cu -- SIR step over cell-ordered records, one fused kernel per step.
 //
-// Layout.  Agents are kept as records sorted by cell (c = y*L + x): rec_id[s]
-// (agent id) and rec_aux[s] (x, state and the agent's draws for the next
-// step, bit layout in amb_internal.cuh).  row_start[r] is the first slot of
+// Layout.  Agents are kept as 8-byte records sorted by cell (c = y*L + x):
+// rec[s] = {agent id, word}, the word holding x, state and the agent's draws
+// for the next step (bit layout in amb_internal.cuh); id and word sit side by
+// side so a record moves with one 64-bit load or store.  row_start[r] is the first slot of
 // grid row r (row_start[L] = n); start[C+1] is the counting-sort cell index
 // (grid environment, paper Sec. 4.1).  y is implied by the row a record sits
 // in, so a record is 8 bytes.
@@ -59,11 +60,9 @@ constexpr int kU2 = 4;                         // independent loads per thread, 
 constexpr uint32_t kNoCode = 255u;             // search result "no k <= 254"
 
 struct BandArgs {
-    const uint32_t *id_in;
-    const uint32_t *aux_in;
+    const uint2 *rec_in;  // {id, word}
     const int32_t *row_in;
-    uint32_t *id_out;
-    uint32_t *aux_out;
+    uint2 *rec_out;
     int32_t *row_out;
     int32_t *start;
     uint32_t *wide;  // 2 * H * L words per CTA, or null when n < kPackedLimit
@@ -165,11 +164,9 @@ __device__ __forceinline__ uint32_t wrap_step(uint32_t v, uint32_t dp, uint32_t 
 // Record word of an agent at column x whose state (after this step) is st,
 // with its draws for step t: the column after its move, the move's dy, and
 // the infection code (susceptible) or recovery bit (infected).
-__device__ __forceinline__ uint32_t record_word(uint32_t id, uint32_t t, uint32_t st, uint32_t x, uint32_t L,
-                                                const uint32_t *rk0, const uint32_t *rk1, const CodeTables &ct,
+__device__ __forceinline__ uint32_t pack_record(const U4 &u, uint32_t st, uint32_t x, uint32_t L, const CodeTables &ct,
                                                 uint32_t K, uint32_t tinf_max, uint32_t t_rec)
 {
-    const U4 u = philox_rk(id, t, rk0, rk1);
     const uint32_t d = u.w0 >> 29;
     uint32_t w = wrap_step(x, (kPackDX >> (2u * d)) & 3u, L) | (st << kAuxStateShift) |
                  (((kPackDY >> (2u * d)) & 3u) << kAuxDyShift);
@@ -178,6 +175,13 @@ __device__ __forceinline__ uint32_t record_word(uint32_t id, uint32_t t, uint32_
     else if (st == AMB_I)
         w |= (u.w2 < t_rec ? 1u : 0u) << kAuxRecShift;
     return w;
+}
+
+__device__ __forceinline__ uint32_t record_word(uint32_t id, uint32_t t, uint32_t st, uint32_t x, uint32_t L,
+                                                const uint32_t *rk0, const uint32_t *rk1, const CodeTables &ct,
+                                                uint32_t K, uint32_t tinf_max, uint32_t t_rec)
+{
+    return pack_record(philox_rk(id, t, rk0, rk1), st, x, L, ct, K, tinf_max, t_rec);
 }
 
 // ------------------------------------------------------------- counters ---
@@ -366,8 +370,7 @@ __device__ __forceinline__ uint32_t new_state(const BandArgs &a, const Ctr &ctr,
 __device__ __forceinline__ void emit(const BandArgs &a, const BandShared &sh, uint32_t slot, uint32_t id, uint32_t xn,
                                      uint32_t st, uint32_t tinf_max)
 {
-    a.id_out[slot] = id;
-    a.aux_out[slot] = record_word(id, a.t + 1u, st, xn, a.L, a.rk0, a.rk1, sh.ct, a.K, tinf_max, a.t_rec);
+    a.rec_out[slot] = make_uint2(id, record_word(id, a.t + 1u, st, xn, a.L, a.rk0, a.rk1, sh.ct, a.K, tinf_max, a.t_rec));
 }
 
 // L2 prefetch of global memory by the bulk-copy engine (16-byte aligned
@@ -377,9 +380,9 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// Warp 0: prefetch into L2 the records (ids and words) of the source rows of
-// band b.  Record arrays are allocated with 4 spare entries, so widening a
-// row's range to 16-byte boundaries stays inside them.
+// Warp 0: prefetch into L2 the records of the source rows of band b.  Record
+// arrays are allocated with 2 spare entries, so widening a row's range to
+// 16-byte boundaries stays inside them.
 __device__ __forceinline__ void prefetch_band(const BandArgs &a, uint32_t b, bool single)
 {
     const uint32_t L = a.L;
@@ -388,12 +391,9 @@ __device__ __forceinline__ void prefetch_band(const BandArgs &a, uint32_t b, boo
     const uint32_t nsrc = single ? L : (r1 - r0) + 2u;
     for (uint32_t j = threadIdx.x; j < nsrc; j += 32u) {
         const uint32_t y = single ? j : (r0 + L - 1u + j) % L;
-        const uint32_t s0 = (uint32_t)a.row_in[y] & ~3u;
-        const uint32_t s1 = ((uint32_t)a.row_in[y + 1] + 3u) & ~3u;
-        if (s1 > s0) {
-            prefetch_l2(a.aux_in + s0, (s1 - s0) * 4u);
-            prefetch_l2(a.id_in + s0, (s1 - s0) * 4u);
-        }
+        const uint32_t s0 = (uint32_t)a.row_in[y] & ~1u;
+        const uint32_t s1 = ((uint32_t)a.row_in[y + 1] + 1u) & ~1u;
+        if (s1 > s0) prefetch_l2(a.rec_in + s0, (s1 - s0) * 8u);
     }
 }
 
@@ -422,7 +422,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
                     while (sh.srow[j + 1] <= v) ++j;
                     const uint32_t s = sh.sbase[j] + (v - sh.srow[j]);
                     yy[u] = sh.ytab[j];
-                    if (s < a.n) aux[u] = __ldg(&a.aux_in[s]);
+                    if (s < a.n) aux[u] = __ldg(&a.rec_in[s].y);
                 }
             }
 #pragma unroll
@@ -476,27 +476,42 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
                     const uint32_t s = sh.sbase[j] + (v - sh.srow[j]);
                     yy[u] = sh.ytab[j];
                     if (s < a.n) {
-                        aux[u] = __ldg(&a.aux_in[s]);
-                        ids[u] = __ldg(&a.id_in[s]);
+                        const uint2 rv = __ldg(&a.rec_in[s]);
+                        ids[u] = rv.x;
+                        aux[u] = rv.y;
                     }
                 }
             }
+            // in phases over the thread's records, so that their Philox
+            // blocks are independent instruction streams
+            uint32_t slot[kU2], st[kU2];
+            bool ok[kU2];
 #pragma unroll
             for (int u = 0; u < kU2; ++u) {
                 const uint32_t w = aux[u];
-                if (w == 0xFFFFFFFFu) continue;
                 const uint32_t xn = w & kAuxXMask;
-                if (xn >= L) continue;
                 const uint32_t yo = (yy[u] >> (8u * ((w >> kAuxDyShift) & 3u))) & 0xFFu;
-                if (yo >= rows) continue;
+                ok[u] = (w != 0xFFFFFFFFu) && (xn < L) && (yo < rows);
                 const uint32_t c = yo * L + xn;
-                const uint32_t st = new_state(a, ctr, c, w, ids[u], tl);
-                const uint32_t slot = P + ctr.take(c);
-                if (slot >= a.n) {
-                    atomicOr(a.err, ERR_OVERFLOW);
-                    continue;
+                st[u] = 0u;
+                slot[u] = 0u;
+                if (ok[u]) {
+                    st[u] = new_state(a, ctr, c, w, ids[u], tl);
+                    slot[u] = P + ctr.take(c);
                 }
-                emit(a, sh, slot, ids[u], xn, st, tinf_max);
+                if (ok[u] && slot[u] >= a.n) {
+                    atomicOr(a.err, ERR_OVERFLOW);
+                    ok[u] = false;
+                }
+            }
+            U4 r[kU2];
+#pragma unroll
+            for (int u = 0; u < kU2; ++u) r[u] = philox_rk(ids[u], a.t + 1u, a.rk0, a.rk1);
+#pragma unroll
+            for (int u = 0; u < kU2; ++u) {
+                if (!ok[u]) continue;
+                a.rec_out[slot[u]] =
+                    make_uint2(ids[u], pack_record(r[u], st[u], aux[u] & kAuxXMask, L, sh.ct, a.K, tinf_max, a.t_rec));
             }
         }
     }
@@ -700,13 +715,11 @@ __global__ void sir_batch_advance(SirJob *__restrict__ jobs, uint32_t n_jobs)
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n_jobs; j += gridDim.x * blockDim.x) {
         BandArgs &a = jobs[j].a;
         if (a.t >= jobs[j].t_end) continue;
-        uint32_t *id = a.id_out, *aux = a.aux_out;
+        uint2 *rec = a.rec_out;
         int32_t *row = a.row_out;
-        a.id_out = const_cast<uint32_t *>(a.id_in);
-        a.aux_out = const_cast<uint32_t *>(a.aux_in);
+        a.rec_out = const_cast<uint2 *>(a.rec_in);
         a.row_out = const_cast<int32_t *>(a.row_in);
-        a.id_in = id;
-        a.aux_in = aux;
+        a.rec_in = rec;
         a.row_in = row;
         a.t += 1u;
         a.row += 4;
@@ -726,11 +739,11 @@ __global__ void code_tables_kernel(const uint32_t *__restrict__ t_inf, uint32_t 
 // ------------------------------------------------------------- set-up ---
 // Records of the agents from id-ordered columns: ids already in cell order.
 struct BuildArgs {
-    const uint32_t *ids;
+    const int32_t *ids;
     const int32_t *x;
     const uint8_t *state;
     uint32_t n, L;
-    uint32_t *aux;
+    uint2 *rec;
     uint32_t t;
     uint32_t rk0[10], rk1[10];
     const uint32_t *t_inf;
@@ -743,10 +756,11 @@ __global__ void band_build_kernel(const BuildArgs a)
     load_code_tables(ct, a.t_inf, a.K);
     const uint32_t tinf_max = a.t_inf[a.K];
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < a.n; s += gridDim.x * blockDim.x) {
-        const uint32_t id = a.ids[s];
+        const uint32_t id = (uint32_t)a.ids[s];
         if (id >= a.n) continue;  // only slots of agents left out of the index
         const uint32_t st = a.state[id];
-        a.aux[s] = record_word(id, a.t, st, (uint32_t)a.x[id], a.L, a.rk0, a.rk1, ct, a.K, tinf_max, a.t_rec);
+        a.rec[s] = make_uint2(id, record_word(id, a.t, st, (uint32_t)a.x[id], a.L, a.rk0, a.rk1, ct, a.K, tinf_max,
+                                              a.t_rec));
     }
 }
 
@@ -757,15 +771,20 @@ __global__ void band_rows_kernel(const int32_t *__restrict__ start, uint32_t L, 
 }
 
 // id-ordered column from the records
-__global__ void band_read_kernel(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ aux,
-                                 const int32_t *__restrict__ row_start, const int32_t *__restrict__ start,
-                                 uint32_t n, uint32_t L, int col, void *__restrict__ out)
+__global__ void band_read_kernel(const uint2 *__restrict__ rec, const int32_t *__restrict__ row_start,
+                                 const int32_t *__restrict__ start, uint32_t n, uint32_t L, int col,
+                                 void *__restrict__ out)
 {
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        const uint32_t id = ids[s];
+        const uint2 r = rec[s];
+        const uint32_t id = r.x;
         if (id >= n) continue;
         if (col == AMB_COL_STATE) {
-            static_cast<uint8_t *>(out)[id] = (uint8_t)((aux[s] >> kAuxStateShift) & 3u);
+            static_cast<uint8_t *>(out)[id] = (uint8_t)((r.y >> kAuxStateShift) & 3u);
+            continue;
+        }
+        if (col == -1) {  // the ids in cell order (the cell index's id list)
+            static_cast<int32_t *>(out)[s] = (int32_t)id;
             continue;
         }
         uint32_t lo = 0, hi = L - 1;  // row: largest r with row_start[r] <= s
@@ -868,37 +887,42 @@ amb_status sir_band_init(amb_pop *pop, const int32_t *x, const int32_t *y, const
     pop->band_smem = g.smem;
     for (int b = 0; b < 2; ++b) {
         // 4 spare entries: L2 prefetches of a row widen it to 16-byte boundaries
-        if (!pop->rec_id[b]) AMB_TRY(dalloc(&pop->rec_id[b], (size_t)n + 4u, s));
-        if (!pop->rec_aux[b]) AMB_TRY(dalloc(&pop->rec_aux[b], (size_t)n + 4u, s));
+        if (!pop->rec[b]) AMB_TRY(dalloc(&pop->rec[b], (size_t)n + 2u, s));
         if (!pop->row_start[b]) AMB_TRY(dalloc(&pop->row_start[b], (size_t)L + 1, s));
     }
     if (!pop->start) AMB_TRY(dalloc(&pop->start, C + 1, s));
     int32_t *cnt = nullptr, *cursor = nullptr;
     AMB_TRY(dalloc(&cnt, C, s));
     AMB_TRY(dalloc(&cursor, C, s));
-    // agents into cell order; the id list becomes rec_id of the new buffer
+    // agents into cell order, then their records into the new buffer
     const int nb = pop->cur ^ 1;
-    amb_status st = launch_cell_index(x, y, n, L, pop->start, (int32_t *)pop->rec_id[nb], cnt, cursor, pop->lb,
-                                      pop->err, s);
+    int32_t *ids = nullptr;
+    amb_status st = dalloc(&ids, n, s);
+    if (st == AMB_OK)
+        st = launch_cell_index(x, y, n, L, pop->start, ids, cnt, cursor, pop->lb, pop->err, s);
     dfree(cnt, s);
     dfree(cursor, s);
-    AMB_TRY(st);
+    if (st != AMB_OK) {
+        dfree(ids, s);
+        return st;
+    }
     if (n) {
         BuildArgs b;
-        b.ids = pop->rec_id[nb];
+        b.ids = ids;
         b.x = x;
         b.state = state;
         b.n = n;
         b.L = L;
-        b.aux = pop->rec_aux[nb];
+        b.rec = pop->rec[nb];
         b.t = (uint32_t)pop->t;
         round_keys(pop->key0, pop->key1, b.rk0, b.rk1);
         b.t_inf = pop->t_inf_d;
         b.K = pop->K;
         b.t_rec = pop->t_rec;
         band_build_kernel<<<grid_for(n, 256, 152u * 8u), 256, 0, s>>>(b);
-        AMB_TRY_CUDA(cudaGetLastError());
     }
+    dfree(ids, s);
+    AMB_TRY_CUDA(cudaGetLastError());
     band_rows_kernel<<<grid_for((uint64_t)L + 1, 256), 256, 0, s>>>(pop->start, L, pop->row_start[nb]);
     AMB_TRY_CUDA(cudaGetLastError());
     pop->cur = nb;
@@ -923,11 +947,9 @@ amb_status sir_band_steps(amb_pop *pop, uint32_t k)
     round_keys(pop->key0, pop->key1, a.rk0, a.rk1);
     for (uint32_t j = 0; j < k; ++j) {
         const int in = pop->cur, out = pop->cur ^ 1;
-        a.id_in = pop->rec_id[in];
-        a.aux_in = pop->rec_aux[in];
+        a.rec_in = pop->rec[in];
         a.row_in = pop->row_start[in];
-        a.id_out = pop->rec_id[out];
-        a.aux_out = pop->rec_aux[out];
+        a.rec_out = pop->rec[out];
         a.row_out = pop->row_start[out];
         a.start = pop->start;
         a.wide = pop->band_wide;
@@ -960,8 +982,7 @@ amb_status sir_band_read(amb_pop *pop, amb_col col, void *dst_dev)
     const uint32_t n = pop->p.n;
     if (n == 0) return AMB_OK;
     band_read_kernel<<<grid_for(n, 256, 152u * 8u), 256, 0, pop->stream>>>(
-        pop->rec_id[pop->cur], pop->rec_aux[pop->cur], pop->row_start[pop->cur], pop->start, n, pop->p.grid_side,
-        (int)col, dst_dev);
+        pop->rec[pop->cur], pop->row_start[pop->cur], pop->start, n, pop->p.grid_side, (int)col, dst_dev);
     AMB_TRY_CUDA(cudaGetLastError());
     return AMB_OK;
 }
@@ -977,8 +998,7 @@ amb_status sir_band_occupancy(amb_pop *pop, int32_t *occ)
 void sir_band_release(amb_pop *pop)
 {
     for (int b = 0; b < 2; ++b) {
-        dfree(pop->rec_id[b], pop->stream);
-        dfree(pop->rec_aux[b], pop->stream);
+        dfree(pop->rec[b], pop->stream);
         dfree(pop->row_start[b], pop->stream);
     }
     dfree(pop->band_wide, pop->stream);
@@ -1043,11 +1063,9 @@ amb_status sir_batch_build(SirBatch &sb, amb_pop **pops, const uint32_t *steps, 
         BandArgs &a = jobs[q].a;
         memset(&a, 0, sizeof(a));
         const int in = p->cur, out = p->cur ^ 1;
-        a.id_in = p->rec_id[in];
-        a.aux_in = p->rec_aux[in];
+        a.rec_in = p->rec[in];
         a.row_in = p->row_start[in];
-        a.id_out = p->rec_id[out];
-        a.aux_out = p->rec_aux[out];
+        a.rec_out = p->rec[out];
         a.row_out = p->row_start[out];
         a.start = p->start;
         a.wide = nullptr;

@@ -103,7 +103,7 @@ def test_job_bytes_host_only():
     C = 408 * 408
     # records, cell index and thresholds at least; creation scratch: columns + counters
     assert r >= 16 * 100_000 + 4 * C + 4 * 100_000
-    assert t == 9 * 100_000 + 8 * C
+    assert t == 13 * 100_000 + 8 * C
     r2, _ = amb.amb_job_bytes(amb.make_job("sir", 200_000, seed=1, steps=100, L=408, beta=0.1, gamma=0.02, n0=100))
     assert r2 > r
     rw, tw = amb.amb_job_bytes(amb.make_job("walk", 100_000, seed=1, steps=100, L=408))
