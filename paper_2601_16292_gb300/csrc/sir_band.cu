@@ -200,37 +200,30 @@ struct PackedCtr {
     __device__ __forceinline__ uint32_t get(uint32_t i) const { return w[i] & 0xFFFFu; }
     __device__ __forceinline__ uint32_t infected(uint32_t c) const { return w[c] >> 16; }
     __device__ __forceinline__ uint32_t take(uint32_t c) const { return atomicAdd(&w[c], 1u) & 0xFFFFu; }
-    // exclusive scan of the counts; the high halves are kept
-    __device__ __forceinline__ uint32_t scan(uint32_t cells, uint32_t *s_warp) const
+    // four consecutive words i0 .. i0+3 (i0 a multiple of 4); words at or
+    // beyond `cells` read as 0 and are not written
+    __device__ __forceinline__ void load4(uint32_t i0, uint32_t cells, uint32_t q[4]) const
     {
-        uint32_t running = 0;
-        for (uint32_t base = 0; base < cells; base += kBandNT * 4u) {
-            const uint32_t i0 = base + threadIdx.x * 4u;
-            uint32_t q[4];
-            if (i0 + 3u < cells) {
-                const uint4 v = *reinterpret_cast<const uint4 *>(&w[i0]);
-                q[0] = v.x; q[1] = v.y; q[2] = v.z; q[3] = v.w;
-            } else {
+        if (i0 + 3u < cells) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(&w[i0]);
+            q[0] = v.x; q[1] = v.y; q[2] = v.z; q[3] = v.w;
+        } else {
 #pragma unroll
-                for (int e = 0; e < 4; ++e) q[e] = (i0 + e < cells) ? w[i0 + e] : 0u;
-            }
-            const uint32_t c0 = q[0] & 0xFFFFu, c1 = q[1] & 0xFFFFu, c2 = q[2] & 0xFFFFu, c3 = q[3] & 0xFFFFu;
-            uint32_t total;
-            const uint32_t ex = block_exclusive_scan<kBandNT>(c0 + c1 + c2 + c3, s_warp, &total);
-            const uint32_t o0 = running + ex, o1 = o0 + c0, o2 = o1 + c1, o3 = o2 + c2;
-            const uint32_t r0 = (q[0] & 0xFFFF0000u) | o0, r1 = (q[1] & 0xFFFF0000u) | o1;
-            const uint32_t r2 = (q[2] & 0xFFFF0000u) | o2, r3 = (q[3] & 0xFFFF0000u) | o3;
-            if (i0 + 3u < cells) {
-                *reinterpret_cast<uint4 *>(&w[i0]) = make_uint4(r0, r1, r2, r3);
-            } else {
-                const uint32_t r[4] = {r0, r1, r2, r3};
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (i0 + e < cells) w[i0 + e] = r[e];
-            }
-            running += total;
+            for (int e = 0; e < 4; ++e) q[e] = (i0 + e < cells) ? w[i0 + e] : 0u;
         }
-        return running;
+    }
+    __device__ __forceinline__ static uint32_t count_of(uint32_t q) { return q & 0xFFFFu; }
+    // the cells' offsets inside the band replace the counts; the high halves stay
+    __device__ __forceinline__ void store4(uint32_t i0, uint32_t cells, const uint32_t q[4], const uint32_t o[4]) const
+    {
+        if (i0 + 3u < cells) {
+            *reinterpret_cast<uint4 *>(&w[i0]) = make_uint4((q[0] & 0xFFFF0000u) | o[0], (q[1] & 0xFFFF0000u) | o[1],
+                                                            (q[2] & 0xFFFF0000u) | o[2], (q[3] & 0xFFFF0000u) | o[3]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (i0 + e < cells) w[i0 + e] = (q[e] & 0xFFFF0000u) | o[e];
+        }
     }
 };
 
@@ -252,19 +245,17 @@ struct WideCtr {
     __device__ __forceinline__ uint32_t get(uint32_t i) const { return cnt[i]; }
     __device__ __forceinline__ uint32_t infected(uint32_t c) const { return inf[c]; }
     __device__ __forceinline__ uint32_t take(uint32_t c) const { return atomicAdd(&cnt[c], 1u); }
-    __device__ __forceinline__ uint32_t scan(uint32_t cells, uint32_t *s_warp) const
+    __device__ __forceinline__ void load4(uint32_t i0, uint32_t cells, uint32_t q[4]) const
     {
-        uint32_t running = 0;
-        for (uint32_t base = 0; base < cells; base += kBandNT) {
-            const uint32_t i = base + threadIdx.x;
-            const uint32_t v = (i < cells) ? cnt[i] : 0u;
-            uint32_t total;
-            const uint32_t ex = block_exclusive_scan<kBandNT>(v, s_warp, &total);
-            if (i < cells) cnt[i] = running + ex;
-            running += total;
-        }
-        __threadfence_block();
-        return running;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) q[e] = (i0 + e < cells) ? cnt[i0 + e] : 0u;
+    }
+    __device__ __forceinline__ static uint32_t count_of(uint32_t q) { return q; }
+    __device__ __forceinline__ void store4(uint32_t i0, uint32_t cells, const uint32_t *, const uint32_t o[4]) const
+    {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (i0 + e < cells) cnt[i0 + e] = o[e];
     }
 };
 
@@ -326,7 +317,7 @@ struct BandShared {
     uint32_t sy[kMaxSrcRows];
     uint32_t ytab[kMaxSrcRows];  // per source row: band row reached with dy = -1, 0, +1 (a byte each, 0xFF = outside)
     uint32_t warp[kBandNT / 32 + 1];
-    uint32_t band, prefix;
+    uint32_t band, prefix, total;
     unsigned long long cnt[4];
 };
 
@@ -442,21 +433,85 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
     }
     __syncthreads();
 
-    const uint32_t T = ctr.scan(cells, sh.warp);
-    if (tid < 32) {
+    // scan of the band's counts: every warp owns a run of consecutive cells
+    // (groups of four); (a) warp totals, (b) warp 0 scans them and gets the
+    // band's first slot P by look-back, (c) every warp turns its counts into
+    // offsets and writes the cell index start[] = P + offset
+    const uint32_t lane = tid & 31u, wid = tid >> 5;
+    const uint32_t quads = (cells + 3u) >> 2, qpw = (quads + 31u) >> 5;
+    const uint32_t q0 = wid * qpw, q1 = min(q0 + qpw, quads);
+    {
+        uint32_t part = 0;
+        for (uint32_t q = q0 + lane; q < q1; q += 32u) {
+            uint32_t c[4];
+            ctr.load4(q * 4u, cells, c);
+            part += Ctr::count_of(c[0]) + Ctr::count_of(c[1]) + Ctr::count_of(c[2]) + Ctr::count_of(c[3]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == 0) sh.warp[wid] = part;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const uint32_t v = sh.warp[lane];
+        uint32_t incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += t;
+        }
+        const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
         const uint32_t P = warp_lookback(a.status, b, a.epoch, T, a.err);
-        if (tid == 0) sh.prefix = P;
+        sh.warp[lane] = incl - v;
+        if (lane == 0) {
+            sh.prefix = P;
+            sh.total = T;
+        }
     }
     __syncthreads();
     const uint32_t P = sh.prefix;
-
-    // cell index and row starts of the band
-    int32_t *start_band = a.start + (size_t)r0 * L;
-    for (uint32_t i = tid; i < cells; i += kBandNT) start_band[i] = (int32_t)(P + ctr.get(i));
+    {
+        int32_t *start_band = a.start + (size_t)r0 * L;
+        const bool vec = (((size_t)r0 * L) & 3u) == 0;  // 16-byte aligned start[] stores
+        uint32_t run = sh.warp[wid];
+        for (uint32_t qb = q0; qb < q1; qb += 32u) {
+            const uint32_t q = qb + lane, i0 = q * 4u;
+            uint32_t c[4] = {0u, 0u, 0u, 0u};
+            if (q < q1) ctr.load4(i0, cells, c);
+            const uint32_t n0 = Ctr::count_of(c[0]), n1 = Ctr::count_of(c[1]), n2 = Ctr::count_of(c[2]);
+            const uint32_t s4 = n0 + n1 + n2 + Ctr::count_of(c[3]);
+            uint32_t incl = s4;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= (uint32_t)o) incl += t;
+            }
+            uint32_t off[4];
+            off[0] = run + incl - s4;
+            off[1] = off[0] + n0;
+            off[2] = off[1] + n1;
+            off[3] = off[2] + n2;
+            if (q < q1) {
+                ctr.store4(i0, cells, c, off);
+                if (vec && i0 + 3u < cells) {
+                    *reinterpret_cast<int4 *>(start_band + i0) =
+                        make_int4((int32_t)(P + off[0]), (int32_t)(P + off[1]), (int32_t)(P + off[2]),
+                                  (int32_t)(P + off[3]));
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (i0 + e < cells) start_band[i0 + e] = (int32_t)(P + off[e]);
+                }
+            }
+            run += __shfl_sync(0xffffffffu, incl, 31);
+        }
+    }
+    __syncthreads();
+    // row starts (before pass 2 moves the offsets on)
     for (uint32_t r = tid; r < rows; r += kBandNT) a.row_out[r0 + r] = (int32_t)(P + ctr.get(r * L));
     if (b == a.n_bands - 1u && tid == 0) {
-        a.start[(size_t)L * L] = (int32_t)(P + T);
-        a.row_out[L] = (int32_t)(P + T);
+        a.start[(size_t)L * L] = (int32_t)(P + sh.total);
+        a.row_out[L] = (int32_t)(P + sh.total);
     }
     __syncthreads();
 
