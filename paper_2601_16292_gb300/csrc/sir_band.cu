@@ -312,10 +312,10 @@ __device__ __forceinline__ uint32_t warp_lookback(uint64_t *status, uint32_t til
 
 struct BandShared {
     CodeTables ct;
-    uint32_t srow[kMaxSrcRows + 1];
-    uint32_t sbase[kMaxSrcRows];
-    uint32_t sy[kMaxSrcRows];
-    uint32_t ytab[kMaxSrcRows];  // per source row: band row reached with dy = -1, 0, +1 (a byte each, 0xFF = outside)
+    // per source row j of the band: {end of its records in the band's source
+    // sequence, slot - sequence index, band row reached with dy = -1, 0, +1
+    // (a byte each, 0xFF = outside), grid row}
+    uint4 rows[kMaxSrcRows];
     uint32_t warp[kBandNT / 32 + 1];
     uint32_t band, prefix, total;
     unsigned long long cnt[4];
@@ -327,7 +327,19 @@ struct Tally {
 
 // State after this step of an agent whose record (or stage) word is w and
 // whose new cell is c of the counters (infected count in the high half).
-template <class Ctr>
+// The agent's Philox block for step t: round keys from the kernel parameters
+// (single-population launches), or derived from the key on the fly (batched
+// launches, whose step descriptor sits in shared memory).
+template <bool kParamKeys>
+__device__ __forceinline__ U4 agent_draws(const BandArgs &a, uint32_t id, uint32_t t)
+{
+    if constexpr (kParamKeys)
+        return philox_rk(id, t, a.rk0, a.rk1);
+    else
+        return philox(id, t, a.k0, a.k1);
+}
+
+template <bool kParamKeys, class Ctr>
 __device__ __forceinline__ uint32_t new_state(const BandArgs &a, const Ctr &ctr, uint32_t c, uint32_t w, uint32_t id,
                                               Tally &tl)
 {
@@ -339,7 +351,7 @@ __device__ __forceinline__ uint32_t new_state(const BandArgs &a, const Ctr &ctr,
             if (k >= code) {
                 bool hit = true;
                 if (code == kCodeExact) {
-                    const U4 q = philox_rk(id, a.t, a.rk0, a.rk1);
+                    const U4 q = agent_draws<kParamKeys>(a, id, a.t);
                     hit = q.w1 < a.t_inf[k < a.K ? k : a.K];
                 }
                 if (hit) {
@@ -355,13 +367,6 @@ __device__ __forceinline__ uint32_t new_state(const BandArgs &a, const Ctr &ctr,
     tl.i += (st == AMB_I);
     tl.r += (st == AMB_R);
     return st;
-}
-
-// Write the agent's record for the next step at `slot` (xn: its column now).
-__device__ __forceinline__ void emit(const BandArgs &a, const BandShared &sh, uint32_t slot, uint32_t id, uint32_t xn,
-                                     uint32_t st, uint32_t tinf_max)
-{
-    a.rec_out[slot] = make_uint2(id, record_word(id, a.t + 1u, st, xn, a.L, a.rk0, a.rk1, sh.ct, a.K, tinf_max, a.t_rec));
 }
 
 // L2 prefetch of global memory by the bulk-copy engine (16-byte aligned
@@ -388,7 +393,7 @@ __device__ __forceinline__ void prefetch_band(const BandArgs &a, uint32_t b, boo
     }
 }
 
-template <class Ctr>
+template <bool kParamKeys, class Ctr>
 __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, const Ctr &ctr, uint32_t b, uint32_t r0,
                                           uint32_t r1, uint32_t M, uint32_t tinf_max, Tally &tl)
 {
@@ -402,6 +407,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
     // pass 1: agents and start-of-step infected per new cell of the band
     {
         uint32_t j = 0;  // source row of the thread's current record (never decreases)
+        uint4 ri = sh.rows[0];
         for (uint32_t v0 = tid; v0 < M; v0 += kBandNT * kU1) {
             uint32_t aux[kU1], yy[kU1];
 #pragma unroll
@@ -410,10 +416,9 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
                 aux[u] = 0xFFFFFFFFu;
                 yy[u] = 0u;
                 if (v < M) {
-                    while (sh.srow[j + 1] <= v) ++j;
-                    const uint32_t s = sh.sbase[j] + (v - sh.srow[j]);
-                    yy[u] = sh.ytab[j];
-                    if (s < a.n) aux[u] = __ldg(&a.rec_in[s].y);
+                    while (ri.x <= v) ri = sh.rows[++j];
+                    yy[u] = ri.z;
+                    aux[u] = __ldg(&a.rec_in[v + ri.y].y);
                 }
             }
 #pragma unroll
@@ -518,6 +523,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
     // pass 2: transitions, next draws, scatter (the records come from L2)
     {
         uint32_t j = 0;
+        uint4 ri = sh.rows[0];
         for (uint32_t v0 = tid; v0 < M; v0 += kBandNT * kU2) {
             uint32_t aux[kU2], yy[kU2], ids[kU2];
 #pragma unroll
@@ -527,14 +533,11 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
                 ids[u] = 0u;
                 yy[u] = 0u;
                 if (v < M) {
-                    while (sh.srow[j + 1] <= v) ++j;
-                    const uint32_t s = sh.sbase[j] + (v - sh.srow[j]);
-                    yy[u] = sh.ytab[j];
-                    if (s < a.n) {
-                        const uint2 rv = __ldg(&a.rec_in[s]);
-                        ids[u] = rv.x;
-                        aux[u] = rv.y;
-                    }
+                    while (ri.x <= v) ri = sh.rows[++j];
+                    yy[u] = ri.z;
+                    const uint2 rv = __ldg(&a.rec_in[v + ri.y]);
+                    ids[u] = rv.x;
+                    aux[u] = rv.y;
                 }
             }
             // in phases over the thread's records, so that their Philox
@@ -551,7 +554,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
                 st[u] = 0u;
                 slot[u] = 0u;
                 if (ok[u]) {
-                    st[u] = new_state(a, ctr, c, w, ids[u], tl);
+                    st[u] = new_state<kParamKeys>(a, ctr, c, w, ids[u], tl);
                     slot[u] = P + ctr.take(c);
                 }
                 if (ok[u] && slot[u] >= a.n) {
@@ -561,7 +564,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
             }
             U4 r[kU2];
 #pragma unroll
-            for (int u = 0; u < kU2; ++u) r[u] = philox_rk(ids[u], a.t + 1u, a.rk0, a.rk1);
+            for (int u = 0; u < kU2; ++u) r[u] = agent_draws<kParamKeys>(a, ids[u], a.t + 1u);
 #pragma unroll
             for (int u = 0; u < kU2; ++u) {
                 if (!ok[u]) continue;
@@ -576,6 +579,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
 // All threads: band b of the step described by `a` (its source-row tables,
 // then band_body with shared-memory or, for very dense bands, global
 // counters).  prefetch: pull band b + gridDim.x into L2 meanwhile.
+template <bool kParamKeys>
 __device__ __forceinline__ void process_band(const BandArgs &a, BandShared &sh, uint32_t *band_smem,
                                              uint32_t *wide_slice, uint32_t b, uint32_t tinf_max, bool prefetch,
                                              Tally &tl)
@@ -606,22 +610,20 @@ __device__ __forceinline__ void process_band(const BandArgs &a, BandShared &sh, 
     uint32_t M;
     const uint32_t off = block_exclusive_scan<kBandNT>(len, sh.warp, &M);
     if (tid < nsrc) {
-        sh.srow[tid] = off;
-        sh.sbase[tid] = beg;
-        sh.sy[tid] = y;
+        // record v of the band's source sequence with off <= v < off + len
+        // sits at slot v + (beg - off) (modulo 2^32)
         uint32_t tab = 0;
         for (uint32_t dp = 0; dp < 3u; ++dp) {
             const uint32_t yo = wrap_step(y, dp, L) - r0;  // wraps above 0xFF when outside
             tab |= (yo < r1 - r0 ? yo : 0xFFu) << (8u * dp);
         }
-        sh.ytab[tid] = tab;
+        sh.rows[tid] = make_uint4(off + len, beg - off, tab, y);
     }
-    if (tid == 0) sh.srow[nsrc] = M;
     __syncthreads();
     if (M < kPackedLimit || wide_slice == nullptr)
-        band_body(a, sh, PackedCtr{band_smem}, b, r0, r1, M, tinf_max, tl);
+        band_body<kParamKeys>(a, sh, PackedCtr{band_smem}, b, r0, r1, M, tinf_max, tl);
     else
-        band_body(a, sh, WideCtr{wide_slice, wide_slice + (size_t)a.H * L}, b, r0, r1, M, tinf_max, tl);
+        band_body<kParamKeys>(a, sh, WideCtr{wide_slice, wide_slice + (size_t)a.H * L}, b, r0, r1, M, tinf_max, tl);
 }
 
 // All threads: add the block's tally to row[0..3] and clear it.
@@ -667,7 +669,7 @@ __global__ void __launch_bounds__(kBandNT, kBandCtasPerSm) sir_band_kernel(const
         __syncthreads();
         const uint32_t b = sh.band;
         if (b >= a.n_bands) break;
-        process_band(a, sh, band_smem, wide_slice, b, tinf_max, true, tl);
+        process_band<true>(a, sh, band_smem, wide_slice, b, tinf_max, true, tl);
     }
     flush_tally(sh, tl, a.row);
 }
@@ -756,7 +758,7 @@ __global__ void __launch_bounds__(kBandNT, kBandCtasPerSm)
         if (live) {
             if (tid == 0) s_prev = j;
             const uint32_t tinf_max = a.t_inf[a.K];
-            process_band(a, sh, band_smem, wide_slice, g - band_prefix[j], tinf_max, false, tl);
+            process_band<false>(a, sh, band_smem, wide_slice, g - band_prefix[j], tinf_max, false, tl);
             flush_tally(sh, tl, a.row);
         }
         __syncthreads();
