@@ -442,8 +442,10 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
     // (groups of four); (a) warp totals, (b) warp 0 scans them and gets the
     // band's first slot P by look-back, (c) every warp turns its counts into
     // offsets and writes the cell index start[] = P + offset
+    constexpr uint32_t kWarps = kBandNT / 32;
+    static_assert(kWarps <= 32, "one warp scans the warp totals");
     const uint32_t lane = tid & 31u, wid = tid >> 5;
-    const uint32_t quads = (cells + 3u) >> 2, qpw = (quads + 31u) >> 5;
+    const uint32_t quads = (cells + 3u) >> 2, qpw = (quads + kWarps - 1u) / kWarps;
     const uint32_t q0 = wid * qpw, q1 = min(q0 + qpw, quads);
     {
         uint32_t part = 0;
@@ -458,7 +460,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
     }
     __syncthreads();
     if (wid == 0) {
-        const uint32_t v = sh.warp[lane];
+        const uint32_t v = lane < kWarps ? sh.warp[lane] : 0u;
         uint32_t incl = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -467,7 +469,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
         }
         const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
         const uint32_t P = warp_lookback(a.status, b, a.epoch, T, a.err);
-        sh.warp[lane] = incl - v;
+        if (lane < kWarps) sh.warp[lane] = incl - v;
         if (lane == 0) {
             sh.prefix = P;
             sh.total = T;
