@@ -57,7 +57,14 @@ def lib():
                                ctypes.POINTER(u64), i64p]
         L.orc_curve_moments.argtypes = [i64p, u32, i64p, u32p, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_double)]
-        for f in ("orc_wealth_step", "orc_walk_step", "orc_sir_thresholds", "orc_sir_step",
+        vp, i64 = ctypes.c_void_p, ctypes.c_int64
+        L.orc_col_map.argtypes = [ctypes.c_int, vp, u32, ctypes.c_int, i64]
+        L.orc_col_map_col.argtypes = [ctypes.c_int, vp, ctypes.c_int, vp, u32, ctypes.c_int]
+        L.orc_where.argtypes = [ctypes.c_int, vp, u32, ctypes.c_int, i64, i32p, u32p]
+        L.orc_view_map.argtypes = [ctypes.c_int, vp, u32, i32p, u32, ctypes.c_int, i64]
+        L.orc_view_draw.argtypes = [i32p, u32, u32, u32, u32, u32, u32, ctypes.c_int, i32p]
+        for f in ("orc_col_map", "orc_col_map_col", "orc_where", "orc_view_map", "orc_view_draw",
+                  "orc_wealth_step", "orc_walk_step", "orc_sir_thresholds", "orc_sir_step",
                   "orc_cell_index", "orc_occupancy", "orc_gini", "orc_curve_moments"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
@@ -204,3 +211,56 @@ class Population:
 
     def counts(self):
         return np.array(self.series, dtype=np.int64).reshape(-1, 4)
+
+
+# ------------------------------------------------------------- view API ----
+OPS = {"set": 0, "add": 1, "sub": 2, "mul": 3, "min": 4, "max": 5}
+CMPS = {"==": 0, "!=": 1, "<": 2, "<=": 3, ">": 4, ">=": 5}
+
+
+def _dtype_code(a):
+    if a.dtype == np.int32:
+        return 0
+    if a.dtype == np.uint8:
+        return 1
+    raise ValueError("columns are int32 or uint8")
+
+
+def col_map(col, op, s):
+    """Full-population view update, in place: col = col OP s."""
+    col = np.ascontiguousarray(col)
+    _check(lib().orc_col_map(_dtype_code(col), col.ctypes.data, col.size, OPS[op], int(s)), "col_map")
+    return col
+
+
+def col_map_col(dst, op, src):
+    """dst = dst OP src, elementwise, in place."""
+    _check(lib().orc_col_map_col(_dtype_code(dst), dst.ctypes.data, _dtype_code(src), src.ctypes.data, dst.size,
+                                 OPS[op]), "col_map_col")
+    return dst
+
+
+def where(col, cmp, s):
+    """Filtered view: ascending ids with col CMP s."""
+    ids = np.zeros(max(col.size, 1), dtype=np.int32)
+    k = np.zeros(1, dtype=np.uint32)
+    _check(lib().orc_where(_dtype_code(col), col.ctypes.data, col.size, CMPS[cmp], int(s), _p(ids, ctypes.c_int32),
+                           _p(k, ctypes.c_uint32)), "where")
+    return ids[:int(k[0])]
+
+
+def view_map(col, ids, op, s):
+    """Update through a view (ids may repeat; applied once per occurrence)."""
+    ids = np.ascontiguousarray(ids, dtype=np.int32)
+    _check(lib().orc_view_map(_dtype_code(col), col.ctypes.data, col.size, _p(ids, ctypes.c_int32), ids.size,
+                              OPS[op], int(s)), "view_map")
+    return col
+
+
+def view_draw(ids, seed, rep, step, word, rng, exclude_self):
+    """One random id per listed id (counter-based; see orc_view_draw)."""
+    ids = np.ascontiguousarray(ids, dtype=np.int32)
+    out = np.zeros(max(ids.size, 1), dtype=np.int32)
+    _check(lib().orc_view_draw(_p(ids, ctypes.c_int32), ids.size, int(seed), int(rep), int(step), int(word), int(rng),
+                               int(bool(exclude_self)), _p(out, ctypes.c_int32)), "view_draw")
+    return out[:ids.size]

@@ -372,3 +372,142 @@ int orc_curve_moments(const int64_t *infected, uint32_t T, int64_t *peak, uint32
     *var = (double)(a - b) / ((double)s0 * (double)s0);
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* View primitives (paper Sec. 3.1 and 3.3, the view API): a column of a    */
+/* population is int32 (dtype 0) or uint8 (dtype 1), indexed by agent id.   */
+/*  - full-population view: every row gets  v = v OP s;                     */
+/*  - filtered view: where(column CMP s) = the ids whose value satisfies    */
+/*    the predicate on the column as it is at that moment, ascending;       */
+/*  - scatter view: a list of ids in which ids may repeat; an update is     */
+/*    applied once per occurrence, so additions accumulate (scatter_add).   */
+/* OP: 0 set, 1 add, 2 sub, 3 mul, 4 min, 5 max.  Arithmetic wraps modulo   */
+/* 2^32 (int32) or 2^8 (uint8); min / max compare signed int32 or unsigned  */
+/* uint8 values; the scalar is reduced to the column's type first (two's    */
+/* complement truncation).  CMP: 0 ==, 1 !=, 2 <, 3 <=, 4 >, 5 >=, comparing */
+/* the value (sign-extended int32 or zero-extended uint8) with the 64-bit   */
+/* scalar as integers.                                                      */
+/* ------------------------------------------------------------------------ */
+#define DT_I32 0
+#define DT_U8 1
+
+static int64_t col_get(int dtype, const void *col, uint32_t i)
+{
+    return dtype == DT_I32 ? (int64_t)((const int32_t *)col)[i] : (int64_t)((const uint8_t *)col)[i];
+}
+
+/* v OP s in the column's type */
+static int64_t apply_op(int dtype, int64_t v, int op, int64_t s)
+{
+    if (dtype == DT_I32) {
+        uint32_t a = (uint32_t)v, b = (uint32_t)s, r;
+        int32_t sa = (int32_t)a, sb = (int32_t)b;
+        switch (op) {
+        case 0: r = b; break;
+        case 1: r = a + b; break;
+        case 2: r = a - b; break;
+        case 3: r = a * b; break;
+        case 4: r = (uint32_t)(sa < sb ? sa : sb); break;
+        default: r = (uint32_t)(sa > sb ? sa : sb); break;
+        }
+        return (int64_t)(int32_t)r;
+    } else {
+        uint8_t a = (uint8_t)v, b = (uint8_t)s, r;
+        switch (op) {
+        case 0: r = b; break;
+        case 1: r = (uint8_t)(a + b); break;
+        case 2: r = (uint8_t)(a - b); break;
+        case 3: r = (uint8_t)(a * b); break;
+        case 4: r = a < b ? a : b; break;
+        default: r = a > b ? a : b; break;
+        }
+        return (int64_t)r;
+    }
+}
+
+static void col_set(int dtype, void *col, uint32_t i, int64_t v)
+{
+    if (dtype == DT_I32)
+        ((int32_t *)col)[i] = (int32_t)v;
+    else
+        ((uint8_t *)col)[i] = (uint8_t)v;
+}
+
+static int valid_dtype_op(int dtype, int op) { return (dtype == DT_I32 || dtype == DT_U8) && op >= 0 && op <= 5; }
+
+/* Full-population view: col[i] = col[i] OP s for every row. */
+int orc_col_map(int dtype, void *col, uint32_t n, int op, int64_t s)
+{
+    if (!valid_dtype_op(dtype, op) || (!col && n)) return ORC_EINVAL;
+    for (uint32_t i = 0; i < n; ++i) col_set(dtype, col, i, apply_op(dtype, col_get(dtype, col, i), op, s));
+    return ORC_OK;
+}
+
+/* Full-population view with a column operand: dst[i] = dst[i] OP src[i]
+ * (src's value taken as an integer, then reduced to dst's type). */
+int orc_col_map_col(int dtype_dst, void *dst, int dtype_src, const void *src, uint32_t n, int op)
+{
+    if (!valid_dtype_op(dtype_dst, op) || (dtype_src != DT_I32 && dtype_src != DT_U8) || (n && (!dst || !src)))
+        return ORC_EINVAL;
+    for (uint32_t i = 0; i < n; ++i)
+        col_set(dtype_dst, dst, i, apply_op(dtype_dst, col_get(dtype_dst, dst, i), op, col_get(dtype_src, src, i)));
+    return ORC_OK;
+}
+
+static int compare(int64_t v, int cmp, int64_t s)
+{
+    switch (cmp) {
+    case 0: return v == s;
+    case 1: return v != s;
+    case 2: return v < s;
+    case 3: return v <= s;
+    case 4: return v > s;
+    default: return v >= s;
+    }
+}
+
+/* Filtered view: the ids i (ascending) with col[i] CMP s. */
+int orc_where(int dtype, const void *col, uint32_t n, int cmp, int64_t s, int32_t *ids, uint32_t *count)
+{
+    if ((dtype != DT_I32 && dtype != DT_U8) || cmp < 0 || cmp > 5 || (n && (!col || !ids)) || !count)
+        return ORC_EINVAL;
+    uint32_t k = 0;
+    for (uint32_t i = 0; i < n; ++i)
+        if (compare(col_get(dtype, col, i), cmp, s)) ids[k++] = (int32_t)i;
+    *count = k;
+    return ORC_OK;
+}
+
+/* Update through a view: for every listed id, in list order,
+ * col[id] = col[id] OP s.  Ids must lie in [0, n). */
+int orc_view_map(int dtype, void *col, uint32_t n, const int32_t *ids, uint32_t k, int op, int64_t s)
+{
+    if (!valid_dtype_op(dtype, op) || (k && (!col || !ids))) return ORC_EINVAL;
+    for (uint32_t j = 0; j < k; ++j)
+        if (ids[j] < 0 || (uint32_t)ids[j] >= n) return ORC_EINVAL;
+    for (uint32_t j = 0; j < k; ++j) {
+        uint32_t i = (uint32_t)ids[j];
+        col_set(dtype, col, i, apply_op(dtype, col_get(dtype, col, i), op, s));
+    }
+    return ORC_OK;
+}
+
+/* Random ids, one per listed id (the paper's random recipient choice, in
+ * the counter-based form): for listed agent i, u = the agent's draw for
+ * `step`, r' = uniform_below(u[word], m) with m = range - 1 when
+ * exclude_self (then r = r' + (r' >= i)) and m = range otherwise (r = r').
+ * exclude_self needs range >= 2; range >= 1 otherwise. */
+int orc_view_draw(const int32_t *ids, uint32_t k, uint32_t seed, uint32_t rep, uint32_t step, uint32_t word,
+                  uint32_t range, int exclude_self, int32_t *out)
+{
+    if (word > 3 || (k && (!ids || !out)) || range < (exclude_self ? 2u : 1u) || range > 0x80000000u)
+        return ORC_EINVAL;
+    for (uint32_t j = 0; j < k; ++j) {
+        uint32_t i = (uint32_t)ids[j], u[4];
+        draw(seed, rep, i, step, u);
+        uint32_t r = uniform_below(u[word], exclude_self ? range - 1u : range);
+        if (exclude_self && r >= i) r += 1;
+        out[j] = (int32_t)r;
+    }
+    return ORC_OK;
+}
