@@ -365,6 +365,81 @@ amb_status amb_server_stats(amb_server *s, amb_server_report *out);
  * job's device memory and the server. */
 amb_status amb_server_destroy(amb_server *s);
 
+/* ------------------------------------------------------------- view API ----
+ * The paper's view API (Sec. 3.1, 3.3) over a device-resident columnar table
+ * of n rows (row = agent id):
+ *  - full-population views: amb_table_map / amb_table_map_col update every
+ *    row of a column ("agents.wealth += 10");
+ *  - filtered views: amb_table_where(col, cmp, s) lists, in ascending order,
+ *    the ids whose value satisfies the predicate at the moment of the call
+ *    ("agents.where(agents.wealth > 0)"); updates through it touch exactly
+ *    those rows;
+ *  - scatter views: id lists in which ids may repeat (amb_view_from_ids,
+ *    amb_view_draw); an update through a scatter view is applied once per
+ *    occurrence, so amb_view_scatter_add accumulates duplicates
+ *    ("agents.at[recipients].scatter_add(wealth=1)").
+ * Columns are int32 or uint8.  Operations: v = v OP s with wrapping
+ * arithmetic in the column's type (the scalar is reduced to that type by
+ * two's-complement truncation); MIN / MAX compare signed int32 or unsigned
+ * uint8 values.  Through a view with repeated ids every operation with one
+ * scalar gives the same result in any order (SET stores s; MUL multiplies
+ * once per occurrence).  Predicates compare the value, as a 64-bit integer,
+ * with the 64-bit scalar.
+ * A view's length stays on the device: view operations are asynchronous on
+ * the table's stream and never wait for the host; amb_view_count and
+ * amb_view_ids synchronise.  Views belong to their table and must be
+ * destroyed before it (amb_table_destroy returns AMB_EBUSY otherwise).
+ */
+typedef enum { AMB_DT_I32 = 0, AMB_DT_U8 = 1 } amb_dtype;
+typedef enum { AMB_OP_SET = 0, AMB_OP_ADD = 1, AMB_OP_SUB = 2, AMB_OP_MUL = 3, AMB_OP_MIN = 4, AMB_OP_MAX = 5 } amb_op;
+typedef enum { AMB_CMP_EQ = 0, AMB_CMP_NE = 1, AMB_CMP_LT = 2, AMB_CMP_LE = 3, AMB_CMP_GT = 4, AMB_CMP_GE = 5 } amb_cmp;
+
+typedef struct amb_table amb_table;
+typedef struct amb_view amb_view;
+
+/* A table of n rows (no columns yet) on cuda_stream; n < 2^31. */
+amb_status amb_table_create(uint32_t n, void *cuda_stream, amb_table **out);
+/* Frees the columns; AMB_EBUSY while views of the table exist. */
+amb_status amb_table_destroy(amb_table *t);
+/* Add a column, every row set to fill (bulk creation, paper Sec. 3.3
+ * add_agents with a scalar broadcast); *col_out = its index.  Names are unique. */
+amb_status amb_table_add_column(amb_table *t, const char *name, amb_dtype dtype, int64_t fill, int *col_out);
+/* Index of a named column (AMB_ENOTFOUND if absent). */
+amb_status amb_table_find_column(amb_table *t, const char *name, int *col_out);
+amb_status amb_table_rows(amb_table *t, uint32_t *n);
+/* Replace / read a whole column (n == rows; int32 or uint8 elements). */
+amb_status amb_table_write(amb_table *t, int col, const void *src, size_t n, int src_on_device);
+amb_status amb_table_read(amb_table *t, int col, void *dst, size_t n, int dst_on_device);
+/* Full-population view: col = col OP scalar. */
+amb_status amb_table_map(amb_table *t, int col, amb_op op, int64_t scalar);
+/* Full-population view with a column operand: dst = dst OP src, row by row
+ * (src's value taken as an integer, then reduced to dst's type). */
+amb_status amb_table_map_col(amb_table *t, int dst, amb_op op, int src);
+/* Filtered view: ascending ids with col CMP scalar (order-preserving stream
+ * compaction).  The view holds up to n ids. */
+amb_status amb_table_where(amb_table *t, int col, amb_cmp cmp, int64_t scalar, amb_view **out);
+/* Scatter view from k caller ids (repeats allowed; every id in [0, n),
+ * else AMB_EINVAL).  Synchronises. */
+amb_status amb_view_from_ids(amb_table *t, const int32_t *ids, size_t k, int ids_on_device, amb_view **out);
+/* Scatter view of random ids, one per id i of v, in v's order: u = Philox
+ * (key (seed, replicate), counter (i, step, 0, 0)), r' = hi32(u[word] * m);
+ * exclude_self: m = range - 1 and r = r' + (r' >= i) (a uniformly chosen other
+ * id, range >= 2); otherwise m = range and r = r' (range >= 1). */
+amb_status amb_view_draw(amb_view *v, uint64_t seed, uint32_t replicate, uint32_t step, uint32_t word, uint32_t range,
+                         int exclude_self, amb_view **out);
+/* Update the rows a view lists: col[id] = col[id] OP scalar per listed id. */
+amb_status amb_view_map(amb_view *v, int col, amb_op op, int64_t scalar);
+/* amb_view_map with AMB_OP_ADD: duplicate ids accumulate. */
+amb_status amb_view_scatter_add(amb_view *v, int col, int64_t value);
+/* Number of ids in the view (synchronises). */
+amb_status amb_view_count(amb_view *v, size_t *count);
+/* The view's ids (min(count, cap) of them) into dst; *count (optional) =
+ * the view's length.  Synchronises. */
+amb_status amb_view_ids(amb_view *v, int32_t *dst, size_t cap, int dst_on_device, size_t *count);
+amb_status amb_view_destroy(amb_view *v);
+/* Wait for the table's stream; report device-side errors of view operations. */
+amb_status amb_table_synchronize(amb_table *t);
+
 /*
  * amb_cell_index without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate

@@ -136,6 +136,24 @@ def lib():
             "amb_server_drain": (st, [vp, ctypes.c_double]),
             "amb_server_stats": (st, [vp, ctypes.POINTER(amb_server_report)]),
             "amb_server_destroy": (st, [vp]),
+            "amb_table_create": (st, [u32, vp, ctypes.POINTER(vp)]),
+            "amb_table_destroy": (st, [vp]),
+            "amb_table_add_column": (st, [vp, ctypes.c_char_p, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_int)]),
+            "amb_table_find_column": (st, [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]),
+            "amb_table_rows": (st, [vp, ctypes.POINTER(u32)]),
+            "amb_table_write": (st, [vp, ctypes.c_int, vp, sz, ctypes.c_int]),
+            "amb_table_read": (st, [vp, ctypes.c_int, vp, sz, ctypes.c_int]),
+            "amb_table_map": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64]),
+            "amb_table_map_col": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+            "amb_table_where": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(vp)]),
+            "amb_view_from_ids": (st, [vp, vp, sz, ctypes.c_int, ctypes.POINTER(vp)]),
+            "amb_view_draw": (st, [vp, u64, u32, u32, u32, u32, ctypes.c_int, ctypes.POINTER(vp)]),
+            "amb_view_map": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64]),
+            "amb_view_scatter_add": (st, [vp, ctypes.c_int, ctypes.c_int64]),
+            "amb_view_count": (st, [vp, ctypes.POINTER(sz)]),
+            "amb_view_ids": (st, [vp, vp, sz, ctypes.c_int, ctypes.POINTER(sz)]),
+            "amb_view_destroy": (st, [vp]),
+            "amb_table_synchronize": (st, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -589,3 +607,131 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------- view API ----
+AMB_DT_I32, AMB_DT_U8 = 0, 1
+DTYPES = {"i32": AMB_DT_I32, "int32": AMB_DT_I32, "u8": AMB_DT_U8, "uint8": AMB_DT_U8}
+OPS = {"set": 0, "add": 1, "sub": 2, "mul": 3, "min": 4, "max": 5}
+CMPS = {"==": 0, "!=": 1, "<": 2, "<=": 3, ">": 4, ">=": 5}
+
+
+class Table:
+    """A device-resident columnar table (amb_table) with named int32 / uint8
+    columns; the view API of the paper (Sec. 3.1, 3.3) on top of it."""
+
+    def __init__(self, n, stream=None):
+        self.n = int(n)
+        h = ctypes.c_void_p()
+        _check(lib().amb_table_create(self.n, _stream_handle(stream), ctypes.byref(h)))
+        self.handle = h
+        self.dtypes = {}
+
+    def add_column(self, name, dtype="i32", fill=0):
+        c = ctypes.c_int()
+        _check(lib().amb_table_add_column(self.handle, name.encode(), DTYPES[dtype], int(fill), ctypes.byref(c)))
+        self.dtypes[name] = DTYPES[dtype]
+        return c.value
+
+    def col(self, name):
+        c = ctypes.c_int()
+        _check(lib().amb_table_find_column(self.handle, name.encode(), ctypes.byref(c)))
+        return c.value
+
+    def write(self, name, values):
+        p, dev, n, _ = _buffer(values)
+        _check(lib().amb_table_write(self.handle, self.col(name), p, n, dev))
+
+    def read(self, name, device="cpu"):
+        import torch
+        dt = torch.uint8 if self.dtypes[name] == AMB_DT_U8 else torch.int32
+        out = torch.empty(self.n, dtype=dt, device=device)
+        p, dev, n, _ = _buffer(out)
+        _check(lib().amb_table_read(self.handle, self.col(name), p, n, dev))
+        return out
+
+    def map(self, name, op, scalar):
+        """Full-population view: column OP= scalar."""
+        _check(lib().amb_table_map(self.handle, self.col(name), OPS[op], int(scalar)))
+
+    def map_col(self, dst, op, src):
+        _check(lib().amb_table_map_col(self.handle, self.col(dst), OPS[op], self.col(src)))
+
+    def where(self, name, cmp, scalar):
+        """Filtered view of the ids with column CMP scalar (ascending)."""
+        h = ctypes.c_void_p()
+        _check(lib().amb_table_where(self.handle, self.col(name), CMPS[cmp], int(scalar), ctypes.byref(h)))
+        return View(self, h)
+
+    def at(self, ids):
+        """Scatter view of the given ids (repeats allowed)."""
+        p, dev, n, _ = _buffer(ids)
+        h = ctypes.c_void_p()
+        _check(lib().amb_view_from_ids(self.handle, p, n, dev, ctypes.byref(h)))
+        return View(self, h)
+
+    def synchronize(self):
+        _check(lib().amb_table_synchronize(self.handle))
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            _check(lib().amb_table_destroy(self.handle))
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class View:
+    """A filtered or scatter view of a Table (amb_view)."""
+
+    def __init__(self, table, handle):
+        self.table = table
+        self.handle = handle
+
+    def map(self, name, op, scalar):
+        _check(lib().amb_view_map(self.handle, self.table.col(name), OPS[op], int(scalar)))
+        return self
+
+    def scatter_add(self, name, value):
+        _check(lib().amb_view_scatter_add(self.handle, self.table.col(name), int(value)))
+        return self
+
+    def draw(self, seed, rep, step, word=0, rng=None, exclude_self=True):
+        h = ctypes.c_void_p()
+        rng = self.table.n if rng is None else rng
+        _check(lib().amb_view_draw(self.handle, int(seed), int(rep), int(step), int(word), int(rng),
+                                   int(bool(exclude_self)), ctypes.byref(h)))
+        return View(self.table, h)
+
+    def count(self):
+        k = ctypes.c_size_t()
+        _check(lib().amb_view_count(self.handle, ctypes.byref(k)))
+        return k.value
+
+    def ids(self):
+        k = self.count()
+        out = np.zeros(max(k, 1), dtype=np.int32)
+        got = ctypes.c_size_t()
+        _check(lib().amb_view_ids(self.handle, ctypes.c_void_p(out.ctypes.data), k, 0, ctypes.byref(got)))
+        return out[:got.value]
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            _check(lib().amb_view_destroy(self.handle))
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

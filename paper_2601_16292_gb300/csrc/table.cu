@@ -1,0 +1,745 @@
+// table.cu -- the view API over a device-resident columnar table (paper
+// Sec. 3.1 and 3.3): full-population views (one elementwise kernel over a
+// column), filtered views (an order-preserving stream compaction of the ids
+// whose value satisfies a predicate: per-thread predicate bits, warp-free
+// popc counts, a block scan and a decoupled look-back across tiles) and
+// scatter views (id lists in which ids repeat; updates through them use
+// atomics, so contributions of repeated ids accumulate).  A view's length
+// lives on the device, so chains of view operations run without host
+// synchronisation; every kernel reads it there.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "amb_internal.cuh"
+
+using namespace amb;
+
+namespace {
+
+struct Column {
+    std::string name;
+    amb_dtype dtype;
+    void *ptr = nullptr;  // int32[n] or uint8[n rounded up to 4]
+};
+
+}  // namespace
+
+struct amb_table {
+    uint32_t n = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<Column> cols;
+    uint32_t *err = nullptr;
+    Lookback lb;
+    int live_views = 0;
+};
+
+struct amb_view {
+    amb_table *t = nullptr;
+    int32_t *ids = nullptr;   // capacity entries
+    uint32_t *count = nullptr;  // device
+    uint32_t capacity = 0;
+    bool unique = false;      // filtered views list every id at most once
+};
+
+namespace {
+
+// ------------------------------------------------------------ operations ---
+template <int OP, class T>
+__device__ __forceinline__ T apply(T a, T b)
+{
+    if constexpr (OP == AMB_OP_SET) return b;
+    if constexpr (OP == AMB_OP_ADD) return (T)(a + b);
+    if constexpr (OP == AMB_OP_SUB) return (T)(a - b);
+    if constexpr (OP == AMB_OP_MUL) return (T)(a * b);
+    if constexpr (OP == AMB_OP_MIN) return a < b ? a : b;
+    return a > b ? a : b;
+}
+
+// int32 arithmetic wraps: do it on the unsigned representation
+template <int OP>
+__device__ __forceinline__ int32_t apply_i32(int32_t a, int32_t b)
+{
+    if constexpr (OP == AMB_OP_MIN || OP == AMB_OP_MAX || OP == AMB_OP_SET) return apply<OP, int32_t>(a, b);
+    return (int32_t)apply<OP, uint32_t>((uint32_t)a, (uint32_t)b);
+}
+
+template <int OP>
+__device__ __forceinline__ uint8_t apply_u8(uint8_t a, uint8_t b)
+{
+    return apply<OP, uint8_t>(a, b);
+}
+
+template <int CMP>
+__device__ __forceinline__ bool compare(int64_t v, int64_t s)
+{
+    if constexpr (CMP == AMB_CMP_EQ) return v == s;
+    if constexpr (CMP == AMB_CMP_NE) return v != s;
+    if constexpr (CMP == AMB_CMP_LT) return v < s;
+    if constexpr (CMP == AMB_CMP_LE) return v <= s;
+    if constexpr (CMP == AMB_CMP_GT) return v > s;
+    return v >= s;
+}
+
+constexpr int kMapNT = 256;
+
+// full-population view, scalar operand: 4 int32 (or 16 uint8) per 16-byte access
+template <int OP>
+__global__ void __launch_bounds__(kMapNT) map_i32_kernel(int32_t *__restrict__ c, uint32_t n, int32_t s)
+{
+    const uint32_t nv = n / 4u;
+    int4 *v = reinterpret_cast<int4 *>(c);
+    for (uint32_t i = blockIdx.x * kMapNT + threadIdx.x; i < nv; i += gridDim.x * kMapNT) {
+        int4 q = v[i];
+        q.x = apply_i32<OP>(q.x, s);
+        q.y = apply_i32<OP>(q.y, s);
+        q.z = apply_i32<OP>(q.z, s);
+        q.w = apply_i32<OP>(q.w, s);
+        v[i] = q;
+    }
+    for (uint32_t i = nv * 4u + blockIdx.x * kMapNT + threadIdx.x; i < n; i += gridDim.x * kMapNT)
+        c[i] = apply_i32<OP>(c[i], s);
+}
+
+template <int OP>
+__global__ void __launch_bounds__(kMapNT) map_u8_kernel(uint8_t *__restrict__ c, uint32_t n, uint8_t s)
+{
+    const uint32_t nv = n / 16u;
+    uint4 *v = reinterpret_cast<uint4 *>(c);
+    for (uint32_t i = blockIdx.x * kMapNT + threadIdx.x; i < nv; i += gridDim.x * kMapNT) {
+        uint4 q = v[i];
+        uint32_t *w = reinterpret_cast<uint32_t *>(&q);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t r = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                r |= (uint32_t)apply_u8<OP>((uint8_t)(w[k] >> (8 * b)), s) << (8 * b);
+            w[k] = r;
+        }
+        v[i] = q;
+    }
+    for (uint32_t i = nv * 16u + blockIdx.x * kMapNT + threadIdx.x; i < n; i += gridDim.x * kMapNT)
+        c[i] = apply_u8<OP>(c[i], s);
+}
+
+// full-population view, column operand (element by element)
+template <int OP, class D, class S>
+__global__ void __launch_bounds__(kMapNT) map_col_kernel(D *__restrict__ d, const S *__restrict__ src, uint32_t n)
+{
+    for (uint32_t i = blockIdx.x * kMapNT + threadIdx.x; i < n; i += gridDim.x * kMapNT) {
+        if constexpr (sizeof(D) == 4)
+            d[i] = apply_i32<OP>(d[i], (int32_t)src[i]);
+        else
+            d[i] = apply_u8<OP>(d[i], (uint8_t)src[i]);
+    }
+}
+
+// ---------------------------------------------------------------- where ---
+constexpr int kWhereNT = 256;
+constexpr int kWhereItems = 16;                       // per thread
+constexpr uint32_t kWhereTile = kWhereNT * kWhereItems;  // 4096 ids per tile
+
+template <int CMP, class T>
+__global__ void __launch_bounds__(kWhereNT) where_kernel(const T *__restrict__ c, uint32_t n, int64_t s,
+                                                          int32_t *__restrict__ ids, uint32_t *__restrict__ count,
+                                                          uint32_t n_tiles, unsigned long long *tickets,
+                                                          uint32_t parity, uint64_t *status, uint32_t epoch,
+                                                          uint32_t *err)
+{
+    __shared__ uint32_t s_tile, s_prefix;
+    __shared__ uint32_t s_warp[kWhereNT / 32 + 1];
+    __shared__ int32_t s_ids[kWhereTile];
+    const uint32_t tid = threadIdx.x;
+    if (blockIdx.x == 0 && tid == 0) tickets[parity ^ 1u] = 0ull;
+    for (;;) {
+        if (tid == 0) s_tile = (uint32_t)atomicAdd(&tickets[parity], 1ull);
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        __syncthreads();
+        if (tile >= n_tiles) break;
+        const uint32_t i0 = tile * kWhereTile + tid * kWhereItems;
+        uint32_t bits = 0;
+        if (i0 + kWhereItems <= n) {
+            if constexpr (sizeof(T) == 4) {
+#pragma unroll
+                for (int q = 0; q < kWhereItems / 4; ++q) {
+                    const int4 v = *reinterpret_cast<const int4 *>(c + i0 + 4 * q);
+                    bits |= (uint32_t)compare<CMP>(v.x, s) << (4 * q);
+                    bits |= (uint32_t)compare<CMP>(v.y, s) << (4 * q + 1);
+                    bits |= (uint32_t)compare<CMP>(v.z, s) << (4 * q + 2);
+                    bits |= (uint32_t)compare<CMP>(v.w, s) << (4 * q + 3);
+                }
+            } else {
+                const uint4 v = *reinterpret_cast<const uint4 *>(c + i0);
+                const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int k = 0; k < 16; ++k) bits |= (uint32_t)compare<CMP>((w[k >> 2] >> (8 * (k & 3))) & 0xFFu, s) << k;
+            }
+        } else {
+            for (uint32_t k = 0; k < (uint32_t)kWhereItems; ++k)
+                if (i0 + k < n && compare<CMP>((int64_t)c[i0 + k], s)) bits |= 1u << k;
+        }
+        uint32_t total;
+        const uint32_t ex = block_exclusive_scan<kWhereNT>(__popc(bits), s_warp, &total);
+        // stage the tile's ids in order, then write them out coalesced
+        uint32_t pos = ex;
+        for (uint32_t b = bits; b; b &= b - 1u) s_ids[pos++] = (int32_t)(i0 + __ffs(b) - 1);
+        if (tid == 0) s_prefix = lookback_exclusive(status, tile, epoch, total, err);
+        __syncthreads();
+        const uint32_t pre = s_prefix;
+        for (uint32_t j = tid; j < total; j += kWhereNT) ids[pre + j] = s_ids[j];
+        if (tile == n_tiles - 1u && tid == 0) *count = pre + total;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------- view update ---
+// Bounded compare-and-swap update of one word (lock-free: a failed attempt
+// means another thread's update went in; the bound only guards against a
+// hardware fault turning it into an endless loop).
+template <class F>
+__device__ __forceinline__ void cas_update(uint32_t *word, F f, uint32_t *err)
+{
+    uint32_t old = *reinterpret_cast<volatile uint32_t *>(word);
+    for (uint32_t attempt = 0; attempt < (1u << 24); ++attempt) {
+        const uint32_t prev = atomicCAS(word, old, f(old));
+        if (prev == old) return;
+        old = prev;
+    }
+    atomicOr(err, ERR_TIMEOUT);
+}
+
+template <int OP, bool UNIQUE>
+__global__ void __launch_bounds__(kMapNT) view_map_i32_kernel(int32_t *__restrict__ c, const int32_t *__restrict__ ids,
+                                                              const uint32_t *__restrict__ count, int32_t s,
+                                                              uint32_t *err)
+{
+    const uint32_t k = *count;
+    for (uint32_t i = blockIdx.x * kMapNT + threadIdx.x; i < k; i += gridDim.x * kMapNT) {
+        const uint32_t id = (uint32_t)ids[i];
+        if constexpr (UNIQUE || OP == AMB_OP_SET) {
+            c[id] = apply_i32<OP>(c[id], s);
+        } else if constexpr (OP == AMB_OP_ADD) {
+            atomicAdd(reinterpret_cast<unsigned int *>(c + id), (unsigned int)s);
+        } else if constexpr (OP == AMB_OP_SUB) {
+            atomicSub(reinterpret_cast<unsigned int *>(c + id), (unsigned int)s);
+        } else if constexpr (OP == AMB_OP_MIN) {
+            atomicMin(c + id, s);
+        } else if constexpr (OP == AMB_OP_MAX) {
+            atomicMax(c + id, s);
+        } else {
+            cas_update(reinterpret_cast<uint32_t *>(c + id),
+                       [s](uint32_t v) { return (uint32_t)apply_i32<OP>((int32_t)v, s); }, err);
+        }
+    }
+}
+
+template <int OP, bool UNIQUE>
+__global__ void __launch_bounds__(kMapNT) view_map_u8_kernel(uint8_t *__restrict__ c, const int32_t *__restrict__ ids,
+                                                             const uint32_t *__restrict__ count, uint8_t s,
+                                                             uint32_t *err)
+{
+    const uint32_t k = *count;
+    for (uint32_t i = blockIdx.x * kMapNT + threadIdx.x; i < k; i += gridDim.x * kMapNT) {
+        const uint32_t id = (uint32_t)ids[i];
+        if constexpr (UNIQUE || OP == AMB_OP_SET) {
+            c[id] = apply_u8<OP>(c[id], s);
+        } else {
+            // the byte's aligned 32-bit word (columns are padded to 4 bytes)
+            const uint32_t sh = 8u * (id & 3u);
+            cas_update(reinterpret_cast<uint32_t *>(c + (id & ~3u)),
+                       [s, sh](uint32_t v) {
+                           const uint8_t r = apply_u8<OP>((uint8_t)(v >> sh), s);
+                           return (v & ~(0xFFu << sh)) | ((uint32_t)r << sh);
+                       },
+                       err);
+        }
+    }
+}
+
+// random ids, one per listed id (counter-based: key (seed, rep), counter (id, step))
+__global__ void __launch_bounds__(kMapNT) view_draw_kernel(const int32_t *__restrict__ ids,
+                                                           const uint32_t *__restrict__ count,
+                                                           int32_t *__restrict__ out, uint32_t *__restrict__ out_count,
+                                                           uint32_t k0, uint32_t k1, uint32_t step, uint32_t word,
+                                                           uint32_t range, int exclude_self)
+{
+    const uint32_t k = *count;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *out_count = k;
+    for (uint32_t i = blockIdx.x * kMapNT + threadIdx.x; i < k; i += gridDim.x * kMapNT) {
+        const uint32_t id = (uint32_t)ids[i];
+        const U4 u = philox(id, step, k0, k1);
+        const uint32_t w = word == 0 ? u.w0 : word == 1 ? u.w1 : word == 2 ? u.w2 : u.w3;
+        uint32_t r = below(w, exclude_self ? range - 1u : range);
+        if (exclude_self) r += (r >= id) ? 1u : 0u;
+        out[i] = (int32_t)r;
+    }
+}
+
+// ids outside [0, n) in a caller-provided list
+__global__ void ids_check_kernel(const int32_t *__restrict__ ids, uint32_t k, uint32_t n, uint32_t *err)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x)
+        if (ids[i] < 0 || (uint32_t)ids[i] >= n) atomicOr(err, ERR_RANGE);
+}
+
+__global__ void fill_kernel(uint8_t *__restrict__ p, size_t bytes, uint32_t word)
+{
+    uint32_t *w = reinterpret_cast<uint32_t *>(p);
+    const size_t nw = bytes / 4u;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nw; i += (size_t)gridDim.x * blockDim.x) w[i] = word;
+}
+
+unsigned map_grid(uint64_t work)
+{
+    return grid_for(work, kMapNT, 152u * 16u);
+}
+
+// ----------------------------------------------------------- dispatch ---
+amb_status bad_op(int op) { return fail(AMB_EINVAL, "unknown operation %d", op); }
+
+amb_status launch_map(const Column &col, uint32_t n, int op, int64_t s, cudaStream_t st)
+{
+    if (n == 0) return AMB_OK;
+    if (col.dtype == AMB_DT_I32) {
+        int32_t *c = static_cast<int32_t *>(col.ptr);
+        const int32_t v = (int32_t)(uint32_t)s;
+        const unsigned g = map_grid(n / 4u + 1u);
+        switch (op) {
+        case AMB_OP_SET: map_i32_kernel<AMB_OP_SET><<<g, kMapNT, 0, st>>>(c, n, v); break;
+        case AMB_OP_ADD: map_i32_kernel<AMB_OP_ADD><<<g, kMapNT, 0, st>>>(c, n, v); break;
+        case AMB_OP_SUB: map_i32_kernel<AMB_OP_SUB><<<g, kMapNT, 0, st>>>(c, n, v); break;
+        case AMB_OP_MUL: map_i32_kernel<AMB_OP_MUL><<<g, kMapNT, 0, st>>>(c, n, v); break;
+        case AMB_OP_MIN: map_i32_kernel<AMB_OP_MIN><<<g, kMapNT, 0, st>>>(c, n, v); break;
+        case AMB_OP_MAX: map_i32_kernel<AMB_OP_MAX><<<g, kMapNT, 0, st>>>(c, n, v); break;
+        default: return bad_op(op);
+        }
+    } else {
+        uint8_t *c = static_cast<uint8_t *>(col.ptr);
+        const uint8_t v = (uint8_t)s;
+        const unsigned g = map_grid(n / 16u + 1u);
+        switch (op) {
+        case AMB_OP_SET: map_u8_kernel<AMB_OP_SET><<<g, kMapNT, 0, st>>>(c, n, v); break;
+        case AMB_OP_ADD: map_u8_kernel<AMB_OP_ADD><<<g, kMapNT, 0, st>>>(c, n, v); break;
+        case AMB_OP_SUB: map_u8_kernel<AMB_OP_SUB><<<g, kMapNT, 0, st>>>(c, n, v); break;
+        case AMB_OP_MUL: map_u8_kernel<AMB_OP_MUL><<<g, kMapNT, 0, st>>>(c, n, v); break;
+        case AMB_OP_MIN: map_u8_kernel<AMB_OP_MIN><<<g, kMapNT, 0, st>>>(c, n, v); break;
+        case AMB_OP_MAX: map_u8_kernel<AMB_OP_MAX><<<g, kMapNT, 0, st>>>(c, n, v); break;
+        default: return bad_op(op);
+        }
+    }
+    AMB_TRY_CUDA(cudaGetLastError());
+    return AMB_OK;
+}
+
+template <class D, class S>
+amb_status launch_map_col_t(D *d, const S *src, uint32_t n, int op, cudaStream_t st)
+{
+    const unsigned g = map_grid(n);
+    switch (op) {
+    case AMB_OP_SET: map_col_kernel<AMB_OP_SET><<<g, kMapNT, 0, st>>>(d, src, n); break;
+    case AMB_OP_ADD: map_col_kernel<AMB_OP_ADD><<<g, kMapNT, 0, st>>>(d, src, n); break;
+    case AMB_OP_SUB: map_col_kernel<AMB_OP_SUB><<<g, kMapNT, 0, st>>>(d, src, n); break;
+    case AMB_OP_MUL: map_col_kernel<AMB_OP_MUL><<<g, kMapNT, 0, st>>>(d, src, n); break;
+    case AMB_OP_MIN: map_col_kernel<AMB_OP_MIN><<<g, kMapNT, 0, st>>>(d, src, n); break;
+    case AMB_OP_MAX: map_col_kernel<AMB_OP_MAX><<<g, kMapNT, 0, st>>>(d, src, n); break;
+    default: return bad_op(op);
+    }
+    AMB_TRY_CUDA(cudaGetLastError());
+    return AMB_OK;
+}
+
+template <class T>
+amb_status launch_where_t(amb_table *t, const T *c, int cmp, int64_t s, amb_view *v)
+{
+    const uint32_t n = t->n;
+    cudaStream_t st = t->stream;
+    if (n == 0) {
+        AMB_TRY_CUDA(cudaMemsetAsync(v->count, 0, sizeof(uint32_t), st));
+        return AMB_OK;
+    }
+    const uint32_t n_tiles = (n + kWhereTile - 1u) / kWhereTile;
+    AMB_TRY(t->lb.ensure(n_tiles, st));
+    uint32_t parity, epoch;
+    t->lb.next(&parity, &epoch);
+    const unsigned g = std::min<uint32_t>(n_tiles, 152u * 8u);
+#define WHERE_CASE(C)                                                                                           \
+    case C:                                                                                                     \
+        where_kernel<C, T><<<g, kWhereNT, 0, st>>>(c, n, s, v->ids, v->count, n_tiles, t->lb.tickets, parity, \
+                                                   t->lb.status, epoch, t->err);                                \
+        break;
+    switch (cmp) {
+        WHERE_CASE(AMB_CMP_EQ)
+        WHERE_CASE(AMB_CMP_NE)
+        WHERE_CASE(AMB_CMP_LT)
+        WHERE_CASE(AMB_CMP_LE)
+        WHERE_CASE(AMB_CMP_GT)
+        WHERE_CASE(AMB_CMP_GE)
+    default: return fail(AMB_EINVAL, "unknown comparison %d", cmp);
+    }
+#undef WHERE_CASE
+    AMB_TRY_CUDA(cudaGetLastError());
+    return AMB_OK;
+}
+
+template <bool UNIQUE>
+amb_status launch_view_map_t(amb_view *v, const Column &col, int op, int64_t s)
+{
+    amb_table *t = v->t;
+    cudaStream_t st = t->stream;
+    if (v->capacity == 0) return AMB_OK;
+    const unsigned g = map_grid(v->capacity);
+#define VM_CASE(K, O, val) \
+    case O: K<O, UNIQUE><<<g, kMapNT, 0, st>>>(c, v->ids, v->count, val, t->err); break;
+    if (col.dtype == AMB_DT_I32) {
+        int32_t *c = static_cast<int32_t *>(col.ptr);
+        const int32_t val = (int32_t)(uint32_t)s;
+        switch (op) {
+            VM_CASE(view_map_i32_kernel, AMB_OP_SET, val)
+            VM_CASE(view_map_i32_kernel, AMB_OP_ADD, val)
+            VM_CASE(view_map_i32_kernel, AMB_OP_SUB, val)
+            VM_CASE(view_map_i32_kernel, AMB_OP_MUL, val)
+            VM_CASE(view_map_i32_kernel, AMB_OP_MIN, val)
+            VM_CASE(view_map_i32_kernel, AMB_OP_MAX, val)
+        default: return bad_op(op);
+        }
+    } else {
+        uint8_t *c = static_cast<uint8_t *>(col.ptr);
+        const uint8_t val = (uint8_t)s;
+        switch (op) {
+            VM_CASE(view_map_u8_kernel, AMB_OP_SET, val)
+            VM_CASE(view_map_u8_kernel, AMB_OP_ADD, val)
+            VM_CASE(view_map_u8_kernel, AMB_OP_SUB, val)
+            VM_CASE(view_map_u8_kernel, AMB_OP_MUL, val)
+            VM_CASE(view_map_u8_kernel, AMB_OP_MIN, val)
+            VM_CASE(view_map_u8_kernel, AMB_OP_MAX, val)
+        default: return bad_op(op);
+        }
+    }
+#undef VM_CASE
+    AMB_TRY_CUDA(cudaGetLastError());
+    return AMB_OK;
+}
+
+amb_status table_error(amb_table *t)
+{
+    uint32_t h = 0;
+    AMB_TRY_CUDA(cudaMemcpyAsync(&h, t->err, sizeof(h), cudaMemcpyDeviceToHost, t->stream));
+    AMB_TRY_CUDA(cudaStreamSynchronize(t->stream));
+    if (h & ERR_TIMEOUT) return fail(AMB_ETIMEOUT, "a bounded device-side wait ran out (error word 0x%x)", h);
+    if (h & ERR_RANGE) return fail(AMB_EINVAL, "an id outside [0, n) was given (error word 0x%x)", h);
+    if (h) return fail(AMB_EINVARIANT, "device error word 0x%x", h);
+    return AMB_OK;
+}
+
+amb_status get_col(amb_table *t, int col, Column **out)
+{
+    if (!t) return fail(AMB_EINVAL, "null table");
+    if (col < 0 || (size_t)col >= t->cols.size()) return fail(AMB_EINVAL, "unknown column %d", col);
+    *out = &t->cols[(size_t)col];
+    return AMB_OK;
+}
+
+size_t col_bytes(amb_dtype dt, uint32_t n)
+{
+    return dt == AMB_DT_I32 ? (size_t)n * 4u : (((size_t)n + 3u) & ~(size_t)3u);
+}
+
+amb_status new_view(amb_table *t, uint32_t capacity, bool unique, amb_view **out)
+{
+    amb_view *v = new (std::nothrow) amb_view();
+    if (!v) return fail(AMB_ENOMEM, "host allocation failed");
+    v->t = t;
+    v->capacity = capacity;
+    v->unique = unique;
+    amb_status st = dalloc(&v->ids, capacity, t->stream);
+    if (st == AMB_OK) st = dalloc(&v->count, 1, t->stream);
+    if (st != AMB_OK) {
+        dfree(v->ids, t->stream);
+        dfree(v->count, t->stream);
+        delete v;
+        return st;
+    }
+    t->live_views += 1;
+    *out = v;
+    return AMB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+amb_status amb_table_create(uint32_t n, void *cuda_stream, amb_table **out)
+{
+    if (!out) return fail(AMB_EINVAL, "null pointer");
+    *out = nullptr;
+    if (n > 0x7FFFFFFFu) return fail(AMB_EINVAL, "n must be < 2^31");
+    amb_table *t = new (std::nothrow) amb_table();
+    if (!t) return fail(AMB_ENOMEM, "host allocation failed");
+    t->n = n;
+    t->stream = (cudaStream_t)cuda_stream;
+    amb_status st = dalloc(&t->err, 1, t->stream);
+    if (st == AMB_OK && cudaMemsetAsync(t->err, 0, sizeof(uint32_t), t->stream) != cudaSuccess)
+        st = fail(AMB_ECUDA, "memset failed");
+    if (st != AMB_OK) {
+        dfree(t->err, t->stream);
+        delete t;
+        return st;
+    }
+    *out = t;
+    return AMB_OK;
+}
+
+amb_status amb_table_destroy(amb_table *t)
+{
+    if (!t) return AMB_OK;
+    if (t->live_views) return fail(AMB_EBUSY, "%d views of this table are still alive", t->live_views);
+    for (Column &c : t->cols) dfree(c.ptr, t->stream);
+    dfree(t->err, t->stream);
+    t->lb.release(t->stream);
+    cudaStreamSynchronize(t->stream);
+    delete t;
+    return AMB_OK;
+}
+
+amb_status amb_table_add_column(amb_table *t, const char *name, amb_dtype dtype, int64_t fill, int *col_out)
+{
+    if (!t || !name || !col_out) return fail(AMB_EINVAL, "null pointer");
+    if (dtype != AMB_DT_I32 && dtype != AMB_DT_U8) return fail(AMB_EINVAL, "unknown dtype %d", (int)dtype);
+    if (!*name) return fail(AMB_EINVAL, "empty column name");
+    for (const Column &c : t->cols)
+        if (c.name == name) return fail(AMB_EINVAL, "column '%s' exists", name);
+    Column c;
+    c.name = name;
+    c.dtype = dtype;
+    const size_t bytes = col_bytes(dtype, t->n);
+    unsigned char *p = nullptr;
+    AMB_TRY(dalloc(&p, bytes, t->stream));
+    c.ptr = p;
+    uint32_t word;
+    if (dtype == AMB_DT_I32) {
+        word = (uint32_t)fill;
+    } else {
+        const uint32_t b = (uint8_t)fill;
+        word = b | (b << 8) | (b << 16) | (b << 24);
+    }
+    if (bytes) {
+        fill_kernel<<<grid_for(bytes / 4u, 256, 152u * 8u), 256, 0, t->stream>>>(p, bytes, word);
+        if (cudaGetLastError() != cudaSuccess) {
+            dfree(c.ptr, t->stream);
+            return fail(AMB_ECUDA, "fill launch failed");
+        }
+    }
+    try {
+        t->cols.push_back(c);
+    } catch (...) {
+        dfree(c.ptr, t->stream);
+        return fail(AMB_ENOMEM, "host allocation failed");
+    }
+    *col_out = (int)t->cols.size() - 1;
+    return AMB_OK;
+}
+
+amb_status amb_table_find_column(amb_table *t, const char *name, int *col_out)
+{
+    if (!t || !name || !col_out) return fail(AMB_EINVAL, "null pointer");
+    for (size_t i = 0; i < t->cols.size(); ++i)
+        if (t->cols[i].name == name) {
+            *col_out = (int)i;
+            return AMB_OK;
+        }
+    return fail(AMB_ENOTFOUND, "no column '%s'", name);
+}
+
+amb_status amb_table_rows(amb_table *t, uint32_t *n)
+{
+    if (!t || !n) return fail(AMB_EINVAL, "null pointer");
+    *n = t->n;
+    return AMB_OK;
+}
+
+amb_status amb_table_write(amb_table *t, int col, const void *src, size_t n, int src_on_device)
+{
+    Column *c = nullptr;
+    AMB_TRY(get_col(t, col, &c));
+    if (n != t->n) return fail(AMB_EINVAL, "column length %zu != n = %u", n, t->n);
+    if (!src && n) return fail(AMB_EINVAL, "null pointer");
+    const size_t bytes = (c->dtype == AMB_DT_I32 ? 4u : 1u) * n;
+    if (bytes)
+        AMB_TRY_CUDA(cudaMemcpyAsync(c->ptr, src, bytes, src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                     t->stream));
+    if (!src_on_device) AMB_TRY_CUDA(cudaStreamSynchronize(t->stream));  // the caller may reuse src
+    return AMB_OK;
+}
+
+amb_status amb_table_read(amb_table *t, int col, void *dst, size_t n, int dst_on_device)
+{
+    Column *c = nullptr;
+    AMB_TRY(get_col(t, col, &c));
+    if (n != t->n) return fail(AMB_EINVAL, "column length %zu != n = %u", n, t->n);
+    if (!dst && n) return fail(AMB_EINVAL, "null pointer");
+    AMB_TRY(table_error(t));
+    const size_t bytes = (c->dtype == AMB_DT_I32 ? 4u : 1u) * n;
+    if (bytes)
+        AMB_TRY_CUDA(cudaMemcpyAsync(dst, c->ptr, bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                     t->stream));
+    AMB_TRY_CUDA(cudaStreamSynchronize(t->stream));
+    return AMB_OK;
+}
+
+amb_status amb_table_map(amb_table *t, int col, amb_op op, int64_t scalar)
+{
+    Column *c = nullptr;
+    AMB_TRY(get_col(t, col, &c));
+    return launch_map(*c, t->n, op, scalar, t->stream);
+}
+
+amb_status amb_table_map_col(amb_table *t, int dst, amb_op op, int src)
+{
+    Column *d = nullptr, *s = nullptr;
+    AMB_TRY(get_col(t, dst, &d));
+    AMB_TRY(get_col(t, src, &s));
+    if (t->n == 0) return AMB_OK;
+    if (d->dtype == AMB_DT_I32 && s->dtype == AMB_DT_I32)
+        return launch_map_col_t(static_cast<int32_t *>(d->ptr), static_cast<const int32_t *>(s->ptr), t->n, op, t->stream);
+    if (d->dtype == AMB_DT_I32)
+        return launch_map_col_t(static_cast<int32_t *>(d->ptr), static_cast<const uint8_t *>(s->ptr), t->n, op, t->stream);
+    if (s->dtype == AMB_DT_I32)
+        return launch_map_col_t(static_cast<uint8_t *>(d->ptr), static_cast<const int32_t *>(s->ptr), t->n, op, t->stream);
+    return launch_map_col_t(static_cast<uint8_t *>(d->ptr), static_cast<const uint8_t *>(s->ptr), t->n, op, t->stream);
+}
+
+amb_status amb_table_where(amb_table *t, int col, amb_cmp cmp, int64_t scalar, amb_view **out)
+{
+    if (!out) return fail(AMB_EINVAL, "null pointer");
+    *out = nullptr;
+    Column *c = nullptr;
+    AMB_TRY(get_col(t, col, &c));
+    if ((int)cmp < 0 || (int)cmp > AMB_CMP_GE) return fail(AMB_EINVAL, "unknown comparison %d", (int)cmp);
+    amb_view *v = nullptr;
+    AMB_TRY(new_view(t, t->n, true, &v));
+    const amb_status st = c->dtype == AMB_DT_I32
+                              ? launch_where_t(t, static_cast<const int32_t *>(c->ptr), cmp, scalar, v)
+                              : launch_where_t(t, static_cast<const uint8_t *>(c->ptr), cmp, scalar, v);
+    if (st != AMB_OK) {
+        amb_view_destroy(v);
+        return st;
+    }
+    *out = v;
+    return AMB_OK;
+}
+
+amb_status amb_view_from_ids(amb_table *t, const int32_t *ids, size_t k, int ids_on_device, amb_view **out)
+{
+    if (!t || !out || (!ids && k)) return fail(AMB_EINVAL, "null pointer");
+    *out = nullptr;
+    if (k > 0x7FFFFFFFu) return fail(AMB_EINVAL, "too many ids");
+    if (!ids_on_device)
+        for (size_t i = 0; i < k; ++i)
+            if (ids[i] < 0 || (uint32_t)ids[i] >= t->n) return fail(AMB_EINVAL, "id %d at %zu outside [0, %u)", ids[i], i, t->n);
+    amb_view *v = nullptr;
+    AMB_TRY(new_view(t, (uint32_t)k, false, &v));
+    const uint32_t kk = (uint32_t)k;
+    amb_status st = AMB_OK;
+    if (k && cudaMemcpyAsync(v->ids, ids, k * sizeof(int32_t), ids_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             t->stream) != cudaSuccess)
+        st = fail(AMB_ECUDA, "id copy failed");
+    if (st == AMB_OK && cudaMemcpyAsync(v->count, &kk, sizeof(kk), cudaMemcpyHostToDevice, t->stream) != cudaSuccess)
+        st = fail(AMB_ECUDA, "count copy failed");
+    if (st == AMB_OK && ids_on_device && k) {
+        ids_check_kernel<<<grid_for(k, 256, 152u * 8u), 256, 0, t->stream>>>(v->ids, kk, t->n, t->err);
+        if (cudaGetLastError() != cudaSuccess) st = fail(AMB_ECUDA, "check launch failed");
+    }
+    if (st == AMB_OK) st = table_error(t);  // also: the host copies are complete
+    if (st != AMB_OK) {
+        // a range error stays recorded in the table's error word
+        amb_view_destroy(v);
+        return st;
+    }
+    *out = v;
+    return AMB_OK;
+}
+
+amb_status amb_view_draw(amb_view *v, uint64_t seed, uint32_t replicate, uint32_t step, uint32_t word, uint32_t range,
+                         int exclude_self, amb_view **out)
+{
+    if (!v || !out) return fail(AMB_EINVAL, "null pointer");
+    *out = nullptr;
+    if (seed > 0xFFFFFFFFull) return fail(AMB_EINVAL, "seed must be < 2^32");
+    if (word > 3) return fail(AMB_EINVAL, "word must be 0..3");
+    if (range > 0x80000000u || range < (exclude_self ? 2u : 1u))
+        return fail(AMB_EINVAL, "range %u out of bounds (exclude_self needs >= 2)", range);
+    amb_table *t = v->t;
+    amb_view *r = nullptr;
+    AMB_TRY(new_view(t, v->capacity, false, &r));
+    if (v->capacity) {
+        view_draw_kernel<<<map_grid(v->capacity), kMapNT, 0, t->stream>>>(v->ids, v->count, r->ids, r->count, (uint32_t)seed,
+                                                                          replicate, step, word, range, exclude_self);
+    } else {
+        cudaMemsetAsync(r->count, 0, sizeof(uint32_t), t->stream);
+    }
+    if (cudaGetLastError() != cudaSuccess) {
+        amb_view_destroy(r);
+        return fail(AMB_ECUDA, "draw launch failed");
+    }
+    *out = r;
+    return AMB_OK;
+}
+
+amb_status amb_view_map(amb_view *v, int col, amb_op op, int64_t scalar)
+{
+    if (!v) return fail(AMB_EINVAL, "null view");
+    Column *c = nullptr;
+    AMB_TRY(get_col(v->t, col, &c));
+    return v->unique ? launch_view_map_t<true>(v, *c, op, scalar) : launch_view_map_t<false>(v, *c, op, scalar);
+}
+
+amb_status amb_view_scatter_add(amb_view *v, int col, int64_t value)
+{
+    return amb_view_map(v, col, AMB_OP_ADD, value);
+}
+
+amb_status amb_view_count(amb_view *v, size_t *count)
+{
+    if (!v || !count) return fail(AMB_EINVAL, "null pointer");
+    uint32_t h = 0;
+    AMB_TRY_CUDA(cudaMemcpyAsync(&h, v->count, sizeof(h), cudaMemcpyDeviceToHost, v->t->stream));
+    AMB_TRY(table_error(v->t));
+    *count = h;
+    return AMB_OK;
+}
+
+amb_status amb_view_ids(amb_view *v, int32_t *dst, size_t cap, int dst_on_device, size_t *count)
+{
+    if (!v || (!dst && cap)) return fail(AMB_EINVAL, "null pointer");
+    size_t k = 0;
+    AMB_TRY(amb_view_count(v, &k));
+    if (count) *count = k;
+    const size_t m = std::min(k, cap);
+    if (m)
+        AMB_TRY_CUDA(cudaMemcpyAsync(dst, v->ids, m * sizeof(int32_t),
+                                     dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, v->t->stream));
+    AMB_TRY_CUDA(cudaStreamSynchronize(v->t->stream));
+    return AMB_OK;
+}
+
+amb_status amb_view_destroy(amb_view *v)
+{
+    if (!v) return AMB_OK;
+    dfree(v->ids, v->t->stream);
+    dfree(v->count, v->t->stream);
+    v->t->live_views -= 1;
+    delete v;
+    return AMB_OK;
+}
+
+amb_status amb_table_synchronize(amb_table *t)
+{
+    if (!t) return fail(AMB_EINVAL, "null table");
+    return table_error(t);
+}
+
+}  // extern "C"
