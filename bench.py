@@ -376,6 +376,78 @@ def serve_bench(amb, torch, stream, rank, world, n_jobs=5000, chunk=32, budget_g
             "unit": "agent-steps/s"}
 
 
+def views_bench(amb, torch, stream, hbm, n=100_000_000, reps=5):
+    """The view API's kernels on a 100M-row table (400 MB per int32 column,
+    larger than L2): achieved algorithmic GB/s per operation (bytes the
+    operation must move: every read and written element once; for id-indexed
+    updates the id and the element's read and write) against the measured
+    copy bandwidth; plus the wealth step written with views (10k agents,
+    100 steps) beside the fused wealth kernel."""
+    import numpy as np
+    t = amb.Table(n, stream)
+    t.add_column("c", "i32", fill=0)
+    rng = np.random.default_rng(5)
+    t.write("c", (rng.integers(0, 2, n, dtype=np.int32) * 2 - 1).astype(np.int32))  # +-1, half positive
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return sorted(ms)[len(ms) // 2]
+
+    out = {}
+    ms = timed(lambda: t.map("c", "mul", 1))
+    out["map_full"] = {"ms": ms, "bytes": 8 * n}
+    # each timed call creates its view and frees it again (stream-ordered)
+    ms = timed(lambda: t.where("c", ">", 0).close())
+    v = t.where("c", ">", 0)
+    k = v.count()
+    out["where"] = {"ms": ms, "bytes": 4 * n + 4 * k, "selected": k}
+    ms = timed(lambda: v.map("c", "mul", 1))
+    out["view_map_filtered"] = {"ms": ms, "bytes": 12 * k}
+    ids = torch.from_numpy(rng.integers(0, n, n // 10, dtype=np.int32)).cuda()
+    torch.cuda.synchronize()
+    sv = t.at(ids)
+    ms = timed(lambda: sv.scatter_add("c", 0))
+    out["scatter_add_random"] = {"ms": ms, "bytes": 12 * (n // 10)}
+    ms = timed(lambda: v.draw(1, 0, 3, 0, n, True).close())
+    out["draw"] = {"ms": ms, "bytes": 8 * k}
+    sv.close()
+    v.close()
+    t.close()
+    for r in out.values():
+        r["gbs"] = r["bytes"] / (r["ms"] / 1e3) / 1e9
+        r["frac"] = r["gbs"] / hbm
+    # the wealth step written with views
+    nw, steps = 10_000, 100
+    tw = amb.Table(nw, stream)
+    tw.add_column("wealth", "i32", fill=1)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for step in range(steps):
+        donors = tw.where("wealth", ">", 0)
+        donors.map("wealth", "sub", 1)
+        rec = donors.draw(0, 0, step, 0, nw, True)
+        rec.scatter_add("wealth", 1)
+        rec.close()
+        donors.close()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    tw.close()
+    out["wealth_by_views_10k_100steps"] = {"ms": ms, "agent_steps_per_s": nw * steps / (ms / 1e3), "launches": 4 * steps}
+    out["table_rows"] = n
+    out["peak_gbs"] = hbm
+    return out
+
+
 def cpu_baseline(budget_s=15.0):
     """The oracle as it stands on one host core: the full 10M-agent SIR
     population, as many whole steps as fit in the budget (at least one)."""
@@ -408,6 +480,7 @@ def gpu_arm(args):
     wealth = None if only_sir else time_model_block(amb, torch, "wealth", WEALTH_CFG, stream, rank)
     walk = None if only_sir else time_model_block(amb, torch, "walk", WALK_CFG, stream, rank)
     sweep = None if only_sir else sweep_bench(amb, torch, stream, rank, world)
+    views = None if only_sir else views_bench(amb, torch, stream, load_peaks()[0])
 
     sampler = ClockSampler(local)
     barrier(world)
@@ -468,6 +541,7 @@ def gpu_arm(args):
         "invariants_ok": bool(inv["ok"]),
         "models": {"wealth_10k_100steps": wealth, "walk_1M_L1000_200steps": walk},
         "sweep_1024_jobs": sweep,
+        "view_api": views,
         "serve_5000_jobs": serve,
     }
     print(json.dumps(line))
@@ -523,7 +597,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="amb", choices=["amb", "reference"])
-    ap.add_argument("--only", default="all", choices=["all", "sir", "sweep", "serve"],
+    ap.add_argument("--only", default="all", choices=["all", "sir", "sweep", "serve", "views"],
                     help="sir: time the SIR step alone (no extras; for profiling); sweep / serve: that part alone")
     ap.add_argument("--serve-jobs", type=int, default=5000)
     ap.add_argument("--serve-chunk", type=int, default=32)
@@ -535,6 +609,12 @@ def main():
         from paper_2601_16292_gb300 import amb
         torch.cuda.set_device(0)
         print(json.dumps(sweep_bench(amb, torch, torch.cuda.Stream(), 0, 1)))
+        return
+    if args.impl == "amb" and args.only == "views":
+        import torch
+        from paper_2601_16292_gb300 import amb
+        torch.cuda.set_device(0)
+        print(json.dumps(views_bench(amb, torch, torch.cuda.Stream(), load_peaks()[0])))
         return
     if args.impl == "amb" and args.only == "serve":
         import torch

@@ -8,6 +8,13 @@
 
 namespace amb {
 
+// The library's stream-ordered memory pool on the current device: freed
+// blocks stay cached in the pool (release threshold: never), so repeated
+// allocations of view buffers, staging buffers and batch tables do not map
+// and unmap device memory each time.  Falls back to the device's default
+// pool if a pool cannot be created.
+cudaMemPool_t library_pool();
+
 // Stream-ordered device allocation helpers; every buffer of a population is
 // allocated and freed on the population's stream.
 template <class T>
@@ -15,7 +22,9 @@ amb_status dalloc(T **p, size_t count, cudaStream_t s)
 {
     *p = nullptr;
     if (count == 0) count = 1;
-    cudaError_t e = cudaMallocAsync((void **)p, count * sizeof(T), s);
+    cudaMemPool_t pool = library_pool();
+    cudaError_t e = pool ? cudaMallocFromPoolAsync((void **)p, count * sizeof(T), pool, s)
+                         : cudaMallocAsync((void **)p, count * sizeof(T), s);
     if (e != cudaSuccess) {
         *p = nullptr;
         (void)cudaGetLastError();

@@ -259,57 +259,6 @@ struct WideCtr {
     }
 };
 
-// Warp 0: publish the band aggregate, walk back 32 predecessors at a time,
-// publish the inclusive prefix, return the exclusive prefix (all lanes).
-// Bounded like lookback_exclusive (timer + shared error word).
-__device__ __forceinline__ uint32_t warp_lookback(uint64_t *status, uint32_t tile, uint32_t epoch, uint32_t aggregate,
-                                                  uint32_t *err)
-{
-    const uint32_t lane = threadIdx.x & 31u;
-    if (tile == 0) {
-        if (lane == 0) status_store(&status[0], status_word(epoch, kFlagPrefix, aggregate));
-        return 0u;
-    }
-    if (lane == 0) status_store(&status[tile], status_word(epoch, kFlagAgg, aggregate));
-    uint32_t excl = 0;
-    int64_t base = (int64_t)tile - 1;
-    uint32_t spins = 0;
-    uint64_t t0 = 0;
-    unsigned backoff = 16;
-    while (base >= 0) {
-        const int64_t j = base - (int64_t)lane;
-        const uint64_t s = (j >= 0) ? status_load(&status[j]) : status_word(epoch, kFlagPrefix, 0u);
-        const uint64_t fl = (s >> 32) & 3ull;
-        const bool ready = ((uint32_t)(s >> 34) == epoch) && fl != 0ull;
-        const uint32_t pm = __ballot_sync(0xffffffffu, ready && fl == kFlagPrefix);
-        const uint32_t rm = __ballot_sync(0xffffffffu, ready);
-        const uint32_t last = pm ? (uint32_t)(__ffs(pm) - 1) : 31u;
-        const uint32_t need = (last == 31u) ? 0xffffffffu : ((1u << (last + 1u)) - 1u);
-        if ((rm & need) == need) {
-            uint32_t v = (lane <= last) ? (uint32_t)s : 0u;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            excl += v;
-            if (pm) break;
-            base -= 32;
-            continue;
-        }
-        if (spins == 0) t0 = global_ns();
-        bool give_up = false;
-        if ((++spins & 15u) == 0u)
-            give_up = (error_word(err) & ERR_TIMEOUT) || (global_ns() - t0 > kSpinLimitNs);
-        give_up = __shfl_sync(0xffffffffu, give_up, 0);
-        if (give_up) {
-            if (lane == 0) atomicOr(err, ERR_TIMEOUT);
-            break;
-        }
-        __nanosleep(backoff);
-        if (backoff < 256) backoff <<= 1;
-    }
-    if (lane == 0) status_store(&status[tile], status_word(epoch, kFlagPrefix, excl + aggregate));
-    return excl;
-}
-
 struct BandShared {
     CodeTables ct;
     // per source row j of the band: {end of its records in the band's source

@@ -187,7 +187,10 @@ __global__ void __launch_bounds__(kWhereNT) where_kernel(const T *__restrict__ c
         // stage the tile's ids in order, then write them out coalesced
         uint32_t pos = ex;
         for (uint32_t b = bits; b; b &= b - 1u) s_ids[pos++] = (int32_t)(i0 + __ffs(b) - 1);
-        if (tid == 0) s_prefix = lookback_exclusive(status, tile, epoch, total, err);
+        if (tid < 32) {
+            const uint32_t pre = warp_lookback(status, tile, epoch, total, err);
+            if (tid == 0) s_prefix = pre;
+        }
         __syncthreads();
         const uint32_t pre = s_prefix;
         for (uint32_t j = tid; j < total; j += kWhereNT) ids[pre + j] = s_ids[j];
