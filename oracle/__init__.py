@@ -63,7 +63,12 @@ def lib():
         L.orc_where.argtypes = [ctypes.c_int, vp, u32, ctypes.c_int, i64, i32p, u32p]
         L.orc_view_map.argtypes = [ctypes.c_int, vp, u32, i32p, u32, ctypes.c_int, i64]
         L.orc_view_draw.argtypes = [i32p, u32, u32, u32, u32, u32, u32, ctypes.c_int, i32p]
-        for f in ("orc_col_map", "orc_col_map_col", "orc_where", "orc_view_map", "orc_view_draw",
+        f32p, f32 = ctypes.POINTER(ctypes.c_float), ctypes.c_float
+        L.orc_cinit_positions.argtypes = [u32, f32, f32, u32, u32, f32p, f32p]
+        L.orc_cinit_positions.restype = None
+        L.orc_cwalk_step.argtypes = [u32, f32, f32, f32, u32, u32, u32, f32p, f32p]
+        L.orc_csir_step.argtypes = [u32, f32, f32, f32, f32, u32, u32, u32, u32p, u32, u32, f32p, f32p, u8p, i32p, i64p]
+        for f in ("orc_cwalk_step", "orc_csir_step", "orc_col_map", "orc_col_map_col", "orc_where", "orc_view_map", "orc_view_draw",
                   "orc_wealth_step", "orc_walk_step", "orc_sir_thresholds", "orc_sir_step",
                   "orc_cell_index", "orc_occupancy", "orc_gini", "orc_curve_moments"):
             getattr(L, f).restype = ctypes.c_int
@@ -264,3 +269,48 @@ def view_draw(ids, seed, rep, step, word, rng, exclude_self):
     _check(lib().orc_view_draw(_p(ids, ctypes.c_int32), ids.size, int(seed), int(rep), int(step), int(word), int(rng),
                                int(bool(exclude_self)), _p(out, ctypes.c_int32)), "view_draw")
     return out[:ids.size]
+
+
+# ------------------------------------------------------ continuous space ----
+class CPopulation:
+    """Oracle population of the continuous-space models ("cwalk", "csir"):
+    float32 positions in [0, w] x [0, h]; see orc_cwalk_step / orc_csir_step."""
+
+    def __init__(self, model, n, seed, rep=0, w=100.0, h=100.0, s=1.0, r=5.0, p=0.1, rec_steps=14, n0=5):
+        if model not in ("cwalk", "csir"):
+            raise ValueError(model)
+        self.model, self.n, self.seed, self.rep = model, int(n), int(seed), int(rep)
+        self.w, self.h, self.s, self.r = float(w), float(h), float(s), float(r)
+        self.rec_steps = int(rec_steps)
+        self.t = 0
+        self.series = []
+        self.x = np.zeros(self.n, dtype=np.float32)
+        self.y = np.zeros(self.n, dtype=np.float32)
+        lib().orc_cinit_positions(self.n, self.w, self.h, self.seed, self.rep, _p(self.x, ctypes.c_float),
+                                  _p(self.y, ctypes.c_float))
+        if model == "csir":
+            self.state = np.zeros(self.n, dtype=np.uint8)
+            lib().orc_init_sir_state(self.n, int(n0), _p(self.state, ctypes.c_uint8))
+            self.days = np.zeros(self.n, dtype=np.int32)
+            self.t_inf, _ = sir_thresholds(p, 0.0, self.n)
+            self.K = self.t_inf.size - 1
+
+    def step(self, k=1):
+        cnt = np.zeros(4, dtype=np.int64)
+        for _ in range(int(k)):
+            if self.model == "cwalk":
+                _check(lib().orc_cwalk_step(self.n, self.w, self.h, self.s, self.seed, self.rep, self.t,
+                                            _p(self.x, ctypes.c_float), _p(self.y, ctypes.c_float)), "cwalk_step")
+                cnt[:] = (self.n, 0, 0, 0)
+            else:
+                _check(lib().orc_csir_step(self.n, self.w, self.h, self.s, self.r, self.seed, self.rep, self.t,
+                                           _p(self.t_inf, ctypes.c_uint32), self.K, self.rec_steps,
+                                           _p(self.x, ctypes.c_float), _p(self.y, ctypes.c_float),
+                                           _p(self.state, ctypes.c_uint8), _p(self.days, ctypes.c_int32),
+                                           _p(cnt, ctypes.c_int64)), "csir_step")
+            self.series.append(cnt.copy())
+            self.t += 1
+        return self
+
+    def counts(self):
+        return np.array(self.series, dtype=np.int64).reshape(-1, 4)

@@ -511,3 +511,100 @@ int orc_view_draw(const int32_t *ids, uint32_t k, uint32_t seed, uint32_t rep, u
     }
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Continuous-space models as the paper states them (Sec. 5.1.2): agents in */
+/* the box [0, w] x [0, h] with float32 positions.                          */
+/*  - random walk: independent uniform x and y displacements, clamped to    */
+/*    the box: dx = s * sunit(u0), dy = s * sunit(u1);                       */
+/*  - SIR: an infected agent infects susceptible agents within distance r;  */
+/*    a susceptible agent with k infected contacts becomes infected iff      */
+/*    u2 < t_inf[min(k, K)] (the thresholds of 1 - (1-p)^k, as for the grid  */
+/*    SIR); an agent recovers after rec_steps steps as infected; with        */
+/*    s > 0 every agent first moves as in the walk.                          */
+/* Every float operation below is one IEEE-754 single-precision operation   */
+/* rounded to nearest (-ffp-contract=off: no fused multiply-add):           */
+/*  unit(u)  = (u >> 8) * 2^-24           in [0, 1), exact;                  */
+/*  sunit(u) = ((u >> 8) - 2^23) * 2^-23  in [-1, 1), exact;                 */
+/*  x0 = w * unit(u0), y0 = h * unit(u1) with the initial draw (step         */
+/*  0xFFFFFFFF); x' = clamp(x + dx, 0, w);                                   */
+/*  contact iff (xi - xj)^2 + (yi - yj)^2 <= r*r, evaluated as written.      */
+/* ------------------------------------------------------------------------ */
+static float unit24(uint32_t u) { return (float)(u >> 8) * 5.9604644775390625e-8f; }
+static float sunit24(uint32_t u) { return (float)((int32_t)(u >> 8) - 8388608) * 1.1920928955078125e-7f; }
+static float clampf(float v, float lo, float hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+void orc_cinit_positions(uint32_t n, float w, float h, uint32_t seed, uint32_t rep, float *x, float *y)
+{
+    for (uint32_t i = 0; i < n; ++i) {
+        uint32_t u[4];
+        draw(seed, rep, i, INIT_STEP, u);
+        x[i] = w * unit24(u[0]);
+        y[i] = h * unit24(u[1]);
+    }
+}
+
+static void cmove(float w, float h, float s, const uint32_t u[4], float *x, float *y)
+{
+    float dx = s * sunit24(u[0]);
+    float dy = s * sunit24(u[1]);
+    *x = clampf(*x + dx, 0.0f, w);
+    *y = clampf(*y + dy, 0.0f, h);
+}
+
+int orc_cwalk_step(uint32_t n, float w, float h, float s, uint32_t seed, uint32_t rep, uint32_t t, float *x, float *y)
+{
+    if (!(w >= 0.0f) || !(h >= 0.0f) || !(s >= 0.0f)) return ORC_EINVAL;
+    for (uint32_t i = 0; i < n; ++i) {
+        uint32_t u[4];
+        draw(seed, rep, i, t, u);
+        cmove(w, h, s, u, &x[i], &y[i]);
+    }
+    return ORC_OK;
+}
+
+int orc_csir_step(uint32_t n, float w, float h, float s, float r, uint32_t seed, uint32_t rep, uint32_t t,
+                  const uint32_t *t_inf, uint32_t K, uint32_t rec_steps, float *x, float *y, uint8_t *state,
+                  int32_t *days, int64_t counts[4])
+{
+    if (!(w >= 0.0f) || !(h >= 0.0f) || !(s >= 0.0f) || !(r >= 0.0f) || rec_steps < 1) return ORC_EINVAL;
+    uint32_t *u2 = (uint32_t *)malloc(sizeof(uint32_t) * ((size_t)n + 1));
+    uint8_t *snap = (uint8_t *)malloc((size_t)n + 1);
+    if (!u2 || !snap) { free(u2); free(snap); return ORC_ENOMEM; }
+    /* 1. draws; moves (all agents) when s > 0 */
+    for (uint32_t i = 0; i < n; ++i) {
+        uint32_t u[4];
+        draw(seed, rep, i, t, u);
+        if (s > 0.0f) cmove(w, h, s, u, &x[i], &y[i]);
+        u2[i] = u[2];
+        snap[i] = state[i];
+    }
+    /* 2. transitions against the start-of-step states, all pairs */
+    const float r2 = r * r;
+    int64_t newinf = 0;
+    for (uint32_t j = 0; j < n; ++j) {
+        if (snap[j] == ST_S) {
+            uint32_t k = 0;
+            for (uint32_t i = 0; i < n; ++i) {
+                if (i == j || snap[i] != ST_I) continue;
+                float dx = x[i] - x[j];
+                float dy = y[i] - y[j];
+                float d2 = dx * dx + dy * dy;
+                if (d2 <= r2) k += 1;
+            }
+            if (k >= 1) {
+                uint32_t kk = (k < K) ? k : K;
+                if (u2[j] < t_inf[kk]) { state[j] = ST_I; days[j] = 0; newinf += 1; }
+            }
+        } else if (snap[j] == ST_I) {
+            days[j] += 1;
+            if ((uint32_t)days[j] >= rec_steps) state[j] = ST_R;
+        }
+    }
+    counts[0] = counts[1] = counts[2] = 0;
+    for (uint32_t i = 0; i < n; ++i) counts[state[i]] += 1;
+    counts[3] = newinf;
+    free(u2);
+    free(snap);
+    return ORC_OK;
+}
