@@ -48,13 +48,20 @@ typedef enum {
     AMB_ENOTFOUND = 8    /* server: unknown ticket */
 } amb_status;
 
-typedef enum { AMB_WEALTH = 0, AMB_WALK = 1, AMB_SIR = 2 } amb_model;
+typedef enum {
+    AMB_WEALTH = 0, /* wealth transfer */
+    AMB_WALK = 1,   /* random walk on an integer torus grid */
+    AMB_SIR = 2,    /* spatial SIR, same-cell contacts on the grid */
+    AMB_CWALK = 3,  /* random walk in continuous space (amb_create_continuous) */
+    AMB_CSIR = 4    /* SIR in continuous space, radius contacts (amb_create_continuous) */
+} amb_model;
 
 typedef enum {
     AMB_COL_WEALTH = 0, /* int32, wealth model */
     AMB_COL_X = 1,      /* int32 in [0, L), walk and SIR */
     AMB_COL_Y = 2,      /* int32 in [0, L), walk and SIR */
-    AMB_COL_STATE = 3   /* uint8: AMB_S, AMB_I or AMB_R, SIR */
+    AMB_COL_STATE = 3,  /* uint8: AMB_S, AMB_I or AMB_R, SIR */
+    AMB_COL_DAYS = 4    /* int32: steps spent infected, continuous SIR */
 } amb_col;
 
 enum { AMB_S = 0, AMB_I = 1, AMB_R = 2 };
@@ -91,6 +98,39 @@ typedef struct amb_pop amb_pop;
  */
 amb_status amb_create(amb_model model, const amb_params *p, uint64_t seed, uint32_t replicate,
                       void *cuda_stream, amb_pop **out);
+
+/*
+ * Continuous-space models as the paper states them (Sec. 5.1.2): agents in
+ * the box [0, width] x [0, height] with float32 positions (columns X and Y
+ * are float32 for these models).
+ *  AMB_CWALK: every step dx, dy = step * sunit(u0), step * sunit(u1), then
+ *    the position is clamped to the box.
+ *  AMB_CSIR: (with step > 0, every agent first moves as in AMB_CWALK); a
+ *    susceptible agent with k agents infected at the start of the step within
+ *    distance radius becomes infected iff u2 < T_inf[min(k, K)], T_inf the
+ *    thresholds of 1 - (1 - p_infect)^k (as for AMB_SIR); an agent infected at
+ *    the start of the step counts one more step infected (column DAYS) and
+ *    recovers when that count reaches recovery_steps.  Agents 0 .. n0-1 start
+ *    infected.
+ * Float arithmetic, each operation one IEEE single-precision operation
+ * rounded to nearest: unit(u) = (u >> 8) 2^-24, sunit(u) = ((u >> 8) - 2^23)
+ * 2^-23; initial x = width * unit(u0), y = height * unit(u1) (step
+ * 0xFFFFFFFF); contact iff (xi - xj)^2 + (yi - yj)^2 <= radius * radius,
+ * evaluated in that order.  Per-step counts: CWALK {n, 0, 0, 0}; CSIR
+ * {S, I, R, new infections}.
+ */
+typedef struct {
+    uint32_t n;
+    float width, height;       /* box; >= 0 */
+    float step;                /* displacement half-width s >= 0 (0: SIR agents do not move) */
+    float radius;              /* CSIR contact radius >= 0 */
+    double p_infect;           /* CSIR per-contact infection probability in [0, 1] */
+    uint32_t recovery_steps;   /* CSIR: >= 1 */
+    uint32_t n_init_infected;  /* CSIR: <= n */
+} amb_cparams;
+
+amb_status amb_create_continuous(amb_model model, const amb_cparams *p, uint64_t seed, uint32_t replicate,
+                                 void *cuda_stream, amb_pop **out);
 
 /* Free everything the population owns (stream-ordered), then synchronise. */
 amb_status amb_destroy(amb_pop *pop);

@@ -19,10 +19,10 @@ AMB_ETIMEOUT, AMB_EBUSY, AMB_EBUDGET, AMB_ENOTFOUND = 5, 6, 7, 8
 STATUS_NAMES = {0: "AMB_OK", 1: "AMB_EINVAL", 2: "AMB_ENOMEM", 3: "AMB_ECUDA", 4: "AMB_EINVARIANT",
                 5: "AMB_ETIMEOUT", 6: "AMB_EBUSY", 7: "AMB_EBUDGET", 8: "AMB_ENOTFOUND"}
 
-AMB_WEALTH, AMB_WALK, AMB_SIR = 0, 1, 2
-MODELS = {"wealth": AMB_WEALTH, "walk": AMB_WALK, "sir": AMB_SIR}
-AMB_COL_WEALTH, AMB_COL_X, AMB_COL_Y, AMB_COL_STATE = 0, 1, 2, 3
-COLUMNS = {"wealth": AMB_COL_WEALTH, "x": AMB_COL_X, "y": AMB_COL_Y, "state": AMB_COL_STATE}
+AMB_WEALTH, AMB_WALK, AMB_SIR, AMB_CWALK, AMB_CSIR = 0, 1, 2, 3, 4
+MODELS = {"wealth": AMB_WEALTH, "walk": AMB_WALK, "sir": AMB_SIR, "cwalk": AMB_CWALK, "csir": AMB_CSIR}
+AMB_COL_WEALTH, AMB_COL_X, AMB_COL_Y, AMB_COL_STATE, AMB_COL_DAYS = 0, 1, 2, 3, 4
+COLUMNS = {"wealth": AMB_COL_WEALTH, "x": AMB_COL_X, "y": AMB_COL_Y, "state": AMB_COL_STATE, "days": AMB_COL_DAYS}
 AMB_S, AMB_I, AMB_R = 0, 1, 2
 AMB_SIR_AUTO, AMB_SIR_GENERIC, AMB_SIR_BAND = 0, 1, 2
 
@@ -51,6 +51,12 @@ class amb_stats(ctypes.Structure):
                 ("peak_infected", ctypes.c_int64), ("peak_step", ctypes.c_uint32), ("curve_mean", ctypes.c_double),
                 ("curve_var", ctypes.c_double), ("final_s", ctypes.c_int64), ("final_i", ctypes.c_int64),
                 ("final_r", ctypes.c_int64), ("max_occupancy", ctypes.c_int32)]
+
+
+class amb_cparams(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32), ("width", ctypes.c_float), ("height", ctypes.c_float), ("step", ctypes.c_float),
+                ("radius", ctypes.c_float), ("p_infect", ctypes.c_double), ("recovery_steps", ctypes.c_uint32),
+                ("n_init_infected", ctypes.c_uint32)]
 
 
 class amb_job(ctypes.Structure):
@@ -102,6 +108,8 @@ def lib():
         sig = {
             "amb_create": (st, [ctypes.c_int, ctypes.POINTER(amb_params), u64, u32, vp, ctypes.POINTER(vp)]),
             "amb_destroy": (st, [vp]),
+            "amb_create_continuous": (st, [ctypes.c_int, ctypes.POINTER(amb_cparams), u64, u32, vp,
+                                           ctypes.POINTER(vp)]),
             "amb_step": (st, [vp, u32]),
             "amb_write_column": (st, [vp, ctypes.c_int, vp, sz, ctypes.c_int]),
             "amb_read_column": (st, [vp, ctypes.c_int, vp, sz, ctypes.c_int]),
@@ -735,3 +743,27 @@ class View:
 
     def __exit__(self, *a):
         self.close()
+
+
+class CPopulation(Population):
+    """Continuous-space population ("cwalk" / "csir"): float32 x, y in
+    [0, w] x [0, h]; see amb_create_continuous."""
+
+    def __init__(self, model, n, seed, rep=0, w=100.0, h=100.0, s=1.0, r=5.0, p=0.1, rec_steps=14, n0=5,
+                 stream=None):
+        self.model = model
+        self.n = int(n)
+        self.L = 0
+        self.cparams = amb_cparams(n=self.n, width=float(w), height=float(h), step=float(s), radius=float(r),
+                                   p_infect=float(p), recovery_steps=int(rec_steps), n_init_infected=int(n0))
+        h_ = ctypes.c_void_p()
+        _check(lib().amb_create_continuous(MODELS[model], ctypes.byref(self.cparams), int(seed), int(rep),
+                                           _stream_handle(stream), ctypes.byref(h_)))
+        self.handle = h_
+
+    def column(self, name, device="cuda"):
+        import torch
+        dt = {"x": torch.float32, "y": torch.float32, "state": torch.uint8, "days": torch.int32}[name]
+        out = torch.empty(self.n, dtype=dt, device=device)
+        amb_read_column(self.handle, name, out)
+        return out

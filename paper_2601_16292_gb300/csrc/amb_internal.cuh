@@ -174,6 +174,7 @@ constexpr uint32_t kCodeTable = 254u;  // entries 1..254 of T_inf cached in shar
 struct amb_pop {
     amb_model model;
     amb_params p;
+    amb_cparams cp{};  // continuous-space models
     uint32_t key0 = 0, key1 = 0;
     cudaStream_t stream = nullptr;
     uint64_t t = 0;          // steps completed
@@ -218,6 +219,22 @@ struct amb_pop {
     int64_t *series = nullptr;
     size_t series_cap = 0;
 
+    // continuous-space models: float positions, days infected, and the
+    // infected agents' positions in cell order (grid of cells wider than r)
+    float *fx = nullptr, *fy = nullptr;
+    int32_t *days = nullptr;
+    int32_t *cell = nullptr;
+    float2 *inf_pos = nullptr;
+
     amb::Lookback lb;
     uint32_t *err = nullptr;  // device error word (sticky)
 };
+
+namespace amb {
+bool is_continuous(const amb_pop *pop);
+amb_status cont_steps(amb_pop *pop, uint32_t k);
+amb_status cont_read_column(amb_pop *pop, amb_col col, void *dst, size_t n, int dst_on_device);
+amb_status cont_write_column(amb_pop *pop, amb_col col, const void *src, size_t n, int src_on_device);
+amb_status cont_bounds(amb_pop *pop, bool *ok);
+void cont_release(amb_pop *pop);
+}  // namespace amb

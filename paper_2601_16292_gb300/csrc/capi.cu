@@ -233,6 +233,7 @@ static void release(amb_pop *pop)
     dfree(pop->start, s);
     dfree(pop->ids, s);
     sir_band_release(pop);
+    cont_release(pop);
     dfree(pop->t_inf_d, s);
     dfree(pop->series, s);
     dfree(pop->err, s);
@@ -289,6 +290,8 @@ cudaMemPool_t library_pool()
 amb_status check_params(amb_model model, const amb_params *p, uint64_t seed)
 {
     if (!p) return fail(AMB_EINVAL, "null pointer");
+    if (model == AMB_CWALK || model == AMB_CSIR)
+        return fail(AMB_EINVAL, "continuous-space models are created by amb_create_continuous (and are not batched)");
     if (model != AMB_WEALTH && model != AMB_WALK && model != AMB_SIR) return fail(AMB_EINVAL, "unknown model %d", (int)model);
     if (seed > 0xFFFFFFFFull) return fail(AMB_EINVAL, "seed must be < 2^32");
     if (p->n > 0x7FFFFFFFu) return fail(AMB_EINVAL, "n must be < 2^31");
@@ -302,6 +305,25 @@ amb_status check_params(amb_model model, const amb_params *p, uint64_t seed)
             return fail(AMB_EINVAL, "beta and gamma must be in [0, 1]");
         if (p->n_init_infected > p->n) return fail(AMB_EINVAL, "n_init_infected > n");
         if (p->variant > AMB_SIR_BAND) return fail(AMB_EINVAL, "unknown SIR variant %u", p->variant);
+    }
+    return AMB_OK;
+}
+
+amb_status check_cparams(amb_model model, const amb_cparams *p, uint64_t seed)
+{
+    if (!p) return fail(AMB_EINVAL, "null pointer");
+    if (model != AMB_CWALK && model != AMB_CSIR) return fail(AMB_EINVAL, "not a continuous-space model: %d", (int)model);
+    if (seed > 0xFFFFFFFFull) return fail(AMB_EINVAL, "seed must be < 2^32");
+    if (p->n > 0x7FFFFFFFu) return fail(AMB_EINVAL, "n must be < 2^31");
+    const float lim = 3.0e38f;
+    if (!(p->width >= 0.0f && p->width <= lim) || !(p->height >= 0.0f && p->height <= lim))
+        return fail(AMB_EINVAL, "the box must have finite sides >= 0");
+    if (!(p->step >= 0.0f && p->step <= lim)) return fail(AMB_EINVAL, "step must be finite and >= 0");
+    if (model == AMB_CSIR) {
+        if (!(p->radius >= 0.0f && p->radius <= lim)) return fail(AMB_EINVAL, "radius must be finite and >= 0");
+        if (!(p->p_infect >= 0.0 && p->p_infect <= 1.0)) return fail(AMB_EINVAL, "p_infect must be in [0, 1]");
+        if (p->recovery_steps < 1) return fail(AMB_EINVAL, "recovery_steps must be >= 1");
+        if (p->n_init_infected > p->n) return fail(AMB_EINVAL, "n_init_infected > n");
     }
     return AMB_OK;
 }
@@ -439,6 +461,8 @@ amb_status amb_step(amb_pop *pop, uint32_t k)
         pop->index_valid = false;
         break;
     case AMB_SIR: st = (pop->path == AMB_SIR_BAND) ? sir_band_steps(pop, k) : sir_generic_steps(pop, k); break;
+    case AMB_CWALK:
+    case AMB_CSIR: st = cont_steps(pop, k); break;
     }
     if (st == AMB_OK) pop->t += k;
     return st;
@@ -448,6 +472,10 @@ amb_status amb_write_column(amb_pop *pop, amb_col col, const void *src, size_t n
 {
     if (!pop || (!src && n)) return fail(AMB_EINVAL, "null pointer");
     if (n != pop->p.n) return fail(AMB_EINVAL, "column length %zu != n = %u", n, pop->p.n);
+    if (is_continuous(pop)) {
+        AMB_TRY(device_error(pop));
+        return cont_write_column(pop, col, src, n, src_on_device);
+    }
     const bool ok_col = (pop->model == AMB_WEALTH && col == AMB_COL_WEALTH) ||
                         (pop->model == AMB_WALK && (col == AMB_COL_X || col == AMB_COL_Y)) ||
                         (pop->model == AMB_SIR && (col == AMB_COL_X || col == AMB_COL_Y || col == AMB_COL_STATE));
@@ -527,6 +555,10 @@ amb_status amb_read_column(amb_pop *pop, amb_col col, void *dst, size_t n, int d
 {
     if (!pop || (!dst && n)) return fail(AMB_EINVAL, "null pointer");
     if (n != pop->p.n) return fail(AMB_EINVAL, "column length %zu != n = %u", n, pop->p.n);
+    if (is_continuous(pop)) {
+        AMB_TRY(device_error(pop));
+        return cont_read_column(pop, col, dst, n, dst_on_device);
+    }
     const bool ok_col = (pop->model == AMB_WEALTH && col == AMB_COL_WEALTH) ||
                         (pop->model == AMB_WALK && (col == AMB_COL_X || col == AMB_COL_Y)) ||
                         (pop->model == AMB_SIR && (col == AMB_COL_X || col == AMB_COL_Y || col == AMB_COL_STATE));
@@ -573,7 +605,7 @@ uint64_t amb_launch_count(const amb_pop *pop) { return pop ? pop->launches : 0; 
 amb_status amb_read_index(amb_pop *pop, int32_t *start, int32_t *ids, int dst_on_device)
 {
     if (!pop || !start || (!ids && pop->p.n)) return fail(AMB_EINVAL, "null pointer");
-    if (pop->model == AMB_WEALTH) return fail(AMB_EINVAL, "the wealth model has no grid");
+    if (pop->model == AMB_WEALTH || is_continuous(pop)) return fail(AMB_EINVAL, "this model has no integer grid");
     const uint64_t C = (uint64_t)pop->p.grid_side * pop->p.grid_side;
     if (C >= 0x80000000ull) return fail(AMB_EINVAL, "index needs L*L < 2^31");
     AMB_TRY(device_error(pop));
@@ -644,6 +676,10 @@ amb_status amb_invariants(amb_pop *pop, amb_invariant_report *out)
         dfree(mm, s);
         dfree(sum, s);
         if (n && hmm[0] < 0) r.nonnegative_ok = 0;
+    } else if (is_continuous(pop)) {
+        bool inside = true;
+        AMB_TRY(cont_bounds(pop, &inside));
+        if (!inside) r.bounds_ok = 0;
     } else {
         unsigned long long *bad = nullptr;
         AMB_TRY(dalloc(&bad, 2, s));
@@ -661,7 +697,9 @@ amb_status amb_invariants(amb_pop *pop, amb_invariant_report *out)
             AMB_TRY(copy_out(pop->start + C, &last, sizeof(last), 0, s));
             if (hb[1] || last != (int32_t)n) r.index_ok = 0;
         }
-        if (pop->model == AMB_SIR) {
+    }
+    if (pop->model == AMB_SIR || pop->model == AMB_CSIR) {
+        {
             int64_t prevR = -1;
             for (uint64_t j = pop->monotone_from; j < pop->t; ++j) {
                 const int64_t *q = &rows[j * 4];
@@ -736,7 +774,7 @@ amb_status amb_stats_compute(amb_pop *pop, amb_stats *out, int64_t *hist, size_t
         }
     } else {
         const uint64_t C = (uint64_t)pop->p.grid_side * pop->p.grid_side;
-        if (C < 0x80000000ull) {
+        if (!is_continuous(pop) && C < 0x80000000ull) {
             int32_t *occ = nullptr, *mx = nullptr;
             AMB_TRY(dalloc(&occ, C, s));
             AMB_TRY(dalloc(&mx, 1, s));
@@ -761,7 +799,7 @@ amb_status amb_stats_compute(amb_pop *pop, amb_stats *out, int64_t *hist, size_t
             dfree(occ, s);
             dfree(mx, s);
         }
-        if (pop->model == AMB_SIR) {
+        if (pop->model == AMB_SIR || pop->model == AMB_CSIR) {
             const uint32_t T = (uint32_t)pop->t;
             long long *cs = nullptr;
             AMB_TRY(dalloc(&cs, 8, s));

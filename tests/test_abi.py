@@ -86,7 +86,7 @@ def _c_layout(tmp_path, structs):
 
 
 def test_binding_structs_match_header_layout(tmp_path):
-    structs = [(n, getattr(amb, n)) for n in ("amb_params", "amb_invariant_report", "amb_stats", "amb_job", "amb_tune",
+    structs = [(n, getattr(amb, n)) for n in ("amb_params", "amb_cparams", "amb_invariant_report", "amb_stats", "amb_job", "amb_tune",
                                               "amb_batch_report")]
     structs += [(n, getattr(amb, n)) for n in ("amb_server_config", "amb_result", "amb_server_report")
                 if hasattr(amb, n)]
