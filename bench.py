@@ -448,6 +448,50 @@ def views_bench(amb, torch, stream, hbm, n=100_000_000, reps=5):
     return out
 
 
+# The paper's own timings of its vectorised implementation (Table 1; laptop
+# CPU, 50 steps, ms), quoted for context beside the same models here.
+PAPER_AMBER_MS = {"wealth": {500: 4.4, 1000: 6.4, 5000: 21.0}, "cwalk": {500: 2.7, 1000: 2.7, 5000: 6.2},
+                  "csir": {500: 95.0, 1000: 119.0, 5000: 687.0}}
+
+
+def paper_models_bench(amb, torch, stream, steps=50, reps=3):
+    """The paper's three benchmark models as the paper states them (Sec.
+    5.1.2): wealth transfer, continuous random walk (100 x 100 box, step 1,
+    clamped), continuous SIR (100 x 100, radius 5, p = 0.1, recovery after 14
+    steps, 5 initial infected), N = 500 / 1,000 / 5,000, 50 steps.  wall_ms:
+    create + 50 steps + read the counts (the paper's whole-run protocol; the
+    median of `reps` runs), device_ms: the steps alone (CUDA events)."""
+    out = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for model in ("wealth", "cwalk", "csir"):
+        for n in (500, 1000, 5000):
+            walls, devs = [], []
+            for rep in range(reps + 1):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                if model == "wealth":
+                    p = amb.Population("wealth", n, seed=0, rep=rep, stream=stream)
+                else:
+                    p = amb.CPopulation(model, n, seed=0, rep=rep, w=100.0, h=100.0, s=1.0 if model == "cwalk" else 0.0,
+                                        r=5.0, p=0.1, rec_steps=14, n0=5, stream=stream)
+                e0.record(stream)
+                amb.amb_step(p.handle, steps)
+                e1.record(stream)
+                p.counts()
+                wall = (time.perf_counter() - t0) * 1e3
+                dev = e0.elapsed_time(e1)
+                p.close()
+                if rep:  # the first run warms up
+                    walls.append(wall)
+                    devs.append(dev)
+            w = sorted(walls)[len(walls) // 2]
+            d = sorted(devs)[len(devs) // 2]
+            out["%s_%d" % (model, n)] = {"wall_ms": w, "device_ms": d,
+                                         "agent_steps_per_s": n * steps / (w / 1e3),
+                                         "paper_amber_cpu_ms": PAPER_AMBER_MS[model][n]}
+    return out
+
+
 def cpu_baseline(budget_s=15.0):
     """The oracle as it stands on one host core: the full 10M-agent SIR
     population, as many whole steps as fit in the budget (at least one)."""
@@ -481,6 +525,7 @@ def gpu_arm(args):
     walk = None if only_sir else time_model_block(amb, torch, "walk", WALK_CFG, stream, rank)
     sweep = None if only_sir else sweep_bench(amb, torch, stream, rank, world)
     views = None if only_sir else views_bench(amb, torch, stream, load_peaks()[0])
+    paper_models = None if only_sir else paper_models_bench(amb, torch, stream)
 
     sampler = ClockSampler(local)
     barrier(world)
@@ -542,6 +587,7 @@ def gpu_arm(args):
         "models": {"wealth_10k_100steps": wealth, "walk_1M_L1000_200steps": walk},
         "sweep_1024_jobs": sweep,
         "view_api": views,
+        "paper_models_50steps": paper_models,
         "serve_5000_jobs": serve,
     }
     print(json.dumps(line))
@@ -597,7 +643,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="amb", choices=["amb", "reference"])
-    ap.add_argument("--only", default="all", choices=["all", "sir", "sweep", "serve", "views"],
+    ap.add_argument("--only", default="all", choices=["all", "sir", "sweep", "serve", "views", "paper"],
                     help="sir: time the SIR step alone (no extras; for profiling); sweep / serve: that part alone")
     ap.add_argument("--serve-jobs", type=int, default=5000)
     ap.add_argument("--serve-chunk", type=int, default=32)
@@ -609,6 +655,12 @@ def main():
         from paper_2601_16292_gb300 import amb
         torch.cuda.set_device(0)
         print(json.dumps(sweep_bench(amb, torch, torch.cuda.Stream(), 0, 1)))
+        return
+    if args.impl == "amb" and args.only == "paper":
+        import torch
+        from paper_2601_16292_gb300 import amb
+        torch.cuda.set_device(0)
+        print(json.dumps(paper_models_bench(amb, torch, torch.cuda.Stream())))
         return
     if args.impl == "amb" and args.only == "views":
         import torch
