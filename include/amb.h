@@ -132,6 +132,15 @@ typedef struct {
 amb_status amb_create_continuous(amb_model model, const amb_cparams *p, uint64_t seed, uint32_t replicate,
                                  void *cuda_stream, amb_pop **out);
 
+/* Set the step index to t (checkpoint / resume): the next amb_step runs step
+ * t with the draws of step t.  Because every random draw is keyed by (seed,
+ * replicate, agent id, step), a population created with the same seed and
+ * replicate, given the columns read from another one after t steps
+ * (amb_write_column) and set to step t, continues bit-identically.  Count rows
+ * of steps not run by this population read as zeros; the invariant checks
+ * start at step t.  Synchronises. */
+amb_status amb_set_step(amb_pop *pop, uint64_t t);
+
 /* Free everything the population owns (stream-ordered), then synchronise. */
 amb_status amb_destroy(amb_pop *pop);
 
@@ -502,6 +511,14 @@ amb_status amb_table_synchronize(amb_table *t);
  */
 amb_status amb_cell_index_noalloc(const int32_t *x, const int32_t *y, uint32_t n, uint32_t L, int32_t *start,
                                   int32_t *ids, void *cuda_stream, int sync);
+
+/* Failure-handling self-check (no counterpart in the paper): one warp waits
+ * in the library's decoupled look-back for a predecessor whose status word
+ * nothing ever sets.  The wait is bounded (2 s), so the kernel gives up, sets
+ * the error word and returns; the call returns AMB_ETIMEOUT, the expected
+ * outcome, with *waited_s the time waited, and the device stays usable.  Any
+ * other status means the bound did not work. */
+amb_status amb_selfcheck_wait_timeout(void *cuda_stream, double *waited_s);
 
 /* Version string of the library build. */
 const char *amb_version(void);

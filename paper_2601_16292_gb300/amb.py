@@ -108,6 +108,8 @@ def lib():
         sig = {
             "amb_create": (st, [ctypes.c_int, ctypes.POINTER(amb_params), u64, u32, vp, ctypes.POINTER(vp)]),
             "amb_destroy": (st, [vp]),
+            "amb_set_step": (st, [vp, u64]),
+            "amb_selfcheck_wait_timeout": (st, [vp, ctypes.POINTER(ctypes.c_double)]),
             "amb_create_continuous": (st, [ctypes.c_int, ctypes.POINTER(amb_cparams), u64, u32, vp,
                                            ctypes.POINTER(vp)]),
             "amb_step": (st, [vp, u32]),
@@ -492,6 +494,9 @@ class Population:
     @property
     def t(self):
         return amb_step_index(self.handle)
+
+    def set_step(self, t):
+        _check(lib().amb_set_step(self.handle, int(t)))
 
     def column(self, name, device="cuda"):
         import torch

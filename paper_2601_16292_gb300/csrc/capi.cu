@@ -468,6 +468,37 @@ amb_status amb_step(amb_pop *pop, uint32_t k)
     return st;
 }
 
+amb_status amb_set_step(amb_pop *pop, uint64_t t)
+{
+    if (!pop) return fail(AMB_EINVAL, "null population");
+    if (t >= (uint64_t)kInitStep) return fail(AMB_EINVAL, "step index must be < 2^32 - 1");
+    AMB_TRY(device_error(pop));
+    cudaStream_t s = pop->stream;
+    AMB_TRY(ensure_series(pop, t));
+    if (t > pop->t)  // rows of steps that were not run here read as zeros
+        AMB_TRY_CUDA(cudaMemsetAsync(pop->series + (size_t)pop->t * 4u, 0, (size_t)(t - pop->t) * 4u * sizeof(int64_t), s));
+    pop->t = t;
+    pop->conservation_from = t;
+    pop->monotone_from = t;
+    amb_status st = AMB_OK;
+    if (uses_band(pop) && pop->p.n) {
+        // the records carry each agent's draws for the next step: redraw them for step t
+        const uint32_t n = pop->p.n;
+        int32_t *x = nullptr, *y = nullptr;
+        uint8_t *state = nullptr;
+        if ((st = dalloc(&x, n, s)) == AMB_OK && (st = dalloc(&y, n, s)) == AMB_OK &&
+            (st = dalloc(&state, n, s)) == AMB_OK && (st = sir_band_read(pop, AMB_COL_X, x)) == AMB_OK &&
+            (st = sir_band_read(pop, AMB_COL_Y, y)) == AMB_OK && (st = sir_band_read(pop, AMB_COL_STATE, state)) == AMB_OK)
+            st = sir_band_init(pop, x, y, state);
+        dfree(x, s);
+        dfree(y, s);
+        dfree(state, s);
+    }
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (st == AMB_OK && e != cudaSuccess) st = fail(AMB_ECUDA, "sync: %s", cudaGetErrorString(e));
+    return st;
+}
+
 amb_status amb_write_column(amb_pop *pop, amb_col col, const void *src, size_t n, int src_on_device)
 {
     if (!pop || (!src && n)) return fail(AMB_EINVAL, "null pointer");
@@ -830,6 +861,52 @@ amb_status amb_stats_compute(amb_pop *pop, amb_stats *out, int64_t *hist, size_t
     if (hist_len) *hist_len = bins_out;
     *out = r;
     return AMB_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// One warp waits in the library's look-back for a predecessor tile that never
+// publishes (its status word stays zero).
+__global__ void wait_selfcheck_kernel(uint64_t *status, uint32_t *err, unsigned long long *ns)
+{
+    const uint64_t t0 = global_ns();
+    (void)warp_lookback(status, 1u, 1u, 1u, err);
+    if (threadIdx.x == 0) *ns = global_ns() - t0;
+}
+}  // namespace
+
+extern "C" {
+
+amb_status amb_selfcheck_wait_timeout(void *cuda_stream, double *waited_s)
+{
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    uint64_t *status = nullptr;
+    uint32_t *err = nullptr;
+    unsigned long long *ns = nullptr;
+    amb_status st = dalloc(&status, 2, s);
+    if (st == AMB_OK) st = dalloc(&err, 1, s);
+    if (st == AMB_OK) st = dalloc(&ns, 1, s);
+    if (st == AMB_OK && (cudaMemsetAsync(status, 0, 2 * sizeof(uint64_t), s) != cudaSuccess ||
+                         cudaMemsetAsync(err, 0, sizeof(uint32_t), s) != cudaSuccess))
+        st = fail(AMB_ECUDA, "memset failed");
+    uint32_t h_err = 0;
+    unsigned long long h_ns = 0;
+    if (st == AMB_OK) {
+        wait_selfcheck_kernel<<<1, 32, 0, s>>>(status, err, ns);
+        if (cudaGetLastError() != cudaSuccess || cudaMemcpyAsync(&h_err, err, sizeof(h_err), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(&h_ns, ns, sizeof(h_ns), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            st = fail(AMB_ECUDA, "self-check kernel failed");
+    }
+    dfree(status, s);
+    dfree(err, s);
+    dfree(ns, s);
+    cudaStreamSynchronize(s);
+    AMB_TRY(st);
+    if (waited_s) *waited_s = (double)h_ns * 1e-9;
+    if (h_err & ERR_TIMEOUT) return fail(AMB_ETIMEOUT, "the wait gave up after %.3f s as designed", (double)h_ns * 1e-9);
+    return fail(AMB_EINVARIANT, "the wait ended without its predecessor and without a timeout");
 }
 
 amb_status amb_cell_index(const int32_t *x, const int32_t *y, uint32_t n, uint32_t L, int32_t *start, int32_t *ids,
