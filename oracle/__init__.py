@@ -68,7 +68,10 @@ def lib():
         L.orc_cinit_positions.restype = None
         L.orc_cwalk_step.argtypes = [u32, f32, f32, f32, u32, u32, u32, f32p, f32p]
         L.orc_csir_step.argtypes = [u32, f32, f32, f32, f32, u32, u32, u32, u32p, u32, u32, f32p, f32p, u8p, i32p, i64p]
-        for f in ("orc_cwalk_step", "orc_csir_step", "orc_col_map", "orc_col_map_col", "orc_where", "orc_view_map", "orc_view_draw",
+        L.orc_log_flush.argtypes = [ctypes.c_int, vp, u32, i32p, i64p, u32]
+        L.orc_grid_walk_step.argtypes = [u32, u32p, ctypes.c_int, ctypes.c_int, u32, ctypes.POINTER(i32p), u32, u32,
+                                         u32]
+        for f in ("orc_log_flush", "orc_grid_walk_step", "orc_cwalk_step", "orc_csir_step", "orc_col_map", "orc_col_map_col", "orc_where", "orc_view_map", "orc_view_draw",
                   "orc_wealth_step", "orc_walk_step", "orc_sir_thresholds", "orc_sir_step",
                   "orc_cell_index", "orc_occupancy", "orc_gini", "orc_curve_moments"):
             getattr(L, f).restype = ctypes.c_int
@@ -314,3 +317,30 @@ class CPopulation:
 
     def counts(self):
         return np.array(self.series, dtype=np.int64).reshape(-1, 4)
+
+
+# ------------------------------------------------------ buffered writes ----
+def log_flush(col, ids, values):
+    """Apply recorded writes (ids[j], values[j]) in order: the last per row wins."""
+    ids = np.ascontiguousarray(ids, dtype=np.int32)
+    values = np.ascontiguousarray(values, dtype=np.int64)
+    _check(lib().orc_log_flush(_dtype_code(col), col.ctypes.data, col.size, _p(ids, ctypes.c_int32),
+                               _p(values, ctypes.c_int64), ids.size), "log_flush")
+    return col
+
+
+# ---------------------------------------------------------- grid walks ----
+def grid_walk_step(coords, sizes, moore, torus, seed, rep, t):
+    """One step of the d-dimensional grid walk on the int32 coordinate arrays
+    (modified in place; see orc_grid_walk_step)."""
+    d = len(coords)
+    sz = np.ascontiguousarray(sizes, dtype=np.uint32)
+    arrs = [np.ascontiguousarray(c, dtype=np.int32) for c in coords]
+    ptrs = (ctypes.POINTER(ctypes.c_int32) * d)(*[_p(a, ctypes.c_int32) for a in arrs])
+    n = arrs[0].size if d else 0
+    _check(lib().orc_grid_walk_step(d, _p(sz, ctypes.c_uint32), int(bool(moore)), int(bool(torus)), n, ptrs,
+                                    int(seed), int(rep), int(t)), "grid_walk_step")
+    for c, a in zip(coords, arrs):
+        if c is not a:
+            c[:] = a
+    return coords

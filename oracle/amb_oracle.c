@@ -608,3 +608,81 @@ int orc_csir_step(uint32_t n, float w, float h, float s, float r, uint32_t seed,
     free(snap);
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Buffered per-agent writes (paper Sec. 3.2.1: per-agent record() calls go */
+/* into a pending-writes buffer flushed by one id-keyed update per step):   */
+/* applying k recorded writes (id, value) to a column in record order, so   */
+/* for every row the last recorded value wins.                              */
+/* ------------------------------------------------------------------------ */
+int orc_log_flush(int dtype, void *col, uint32_t n, const int32_t *ids, const int64_t *values, uint32_t k)
+{
+    if ((dtype != DT_I32 && dtype != DT_U8) || (k && (!col || !ids || !values))) return ORC_EINVAL;
+    for (uint32_t j = 0; j < k; ++j)
+        if (ids[j] < 0 || (uint32_t)ids[j] >= n) return ORC_EINVAL;
+    for (uint32_t j = 0; j < k; ++j) col_set(dtype, col, (uint32_t)ids[j], apply_op(dtype, 0, 0, values[j]));
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Grid environments (paper Sec. 4.1): d-dimensional lattices (d = 1..4)    */
+/* with Moore or von Neumann neighbourhoods, on a torus or in a bounded box. */
+/* One step: every agent moves to a neighbour chosen uniformly among its    */
+/* neighbours: m = hi32(u0 * count), the m-th neighbour in this order:      */
+/*  - Moore: offsets in {-1, 0, 1}^d without the zero offset, enumerated as */
+/*    base-3 numbers with dimension 0 the fastest digit (digit - 1 = offset);*/
+/*  - von Neumann: (dim 0, -1), (dim 0, +1), (dim 1, -1), (dim 1, +1), ...; */
+/* on a torus every neighbour exists (coordinates wrap); in a bounded box    */
+/* only neighbours inside the box count, in the same order (an agent with  */
+/* none stays).  For d = 2, Moore, torus this is the random walk above.    */
+/* ------------------------------------------------------------------------ */
+int orc_grid_walk_step(uint32_t d, const uint32_t *sizes, int moore, int torus, uint32_t n, int32_t **coords,
+                       uint32_t seed, uint32_t rep, uint32_t t)
+{
+    if (d < 1 || d > 4) return ORC_EINVAL;
+    for (uint32_t a = 0; a < d; ++a)
+        if (sizes[a] < 1 || sizes[a] > 0x7FFFFFFFu) return ORC_EINVAL;
+    uint32_t full = 1;
+    for (uint32_t a = 0; a < d; ++a) full *= 3u;
+    for (uint32_t i = 0; i < n; ++i) {
+        int32_t c[4] = {0, 0, 0, 0};
+        for (uint32_t a = 0; a < d; ++a) {
+            c[a] = coords[a][i];
+            if (c[a] < 0 || (uint32_t)c[a] >= sizes[a]) return ORC_EINVAL;
+        }
+        /* list this agent's neighbours in order */
+        int32_t off[81][4];
+        uint32_t cnt = 0;
+        if (moore) {
+            for (uint32_t m = 0; m < full; ++m) {
+                uint32_t r = m, zero = 1, inside = 1;
+                int32_t o[4] = {0, 0, 0, 0};
+                for (uint32_t a = 0; a < d; ++a) {
+                    o[a] = (int32_t)(r % 3u) - 1;
+                    r /= 3u;
+                    if (o[a] != 0) zero = 0;
+                    int64_t v = (int64_t)c[a] + o[a];
+                    if (v < 0 || v >= (int64_t)sizes[a]) inside = 0;
+                }
+                if (zero || (!torus && !inside)) continue;
+                for (uint32_t a = 0; a < 4; ++a) off[cnt][a] = o[a];
+                ++cnt;
+            }
+        } else {
+            for (uint32_t a = 0; a < d; ++a)
+                for (int s = -1; s <= 1; s += 2) {
+                    int64_t v = (int64_t)c[a] + s;
+                    if (!torus && (v < 0 || v >= (int64_t)sizes[a])) continue;
+                    for (uint32_t b = 0; b < 4; ++b) off[cnt][b] = 0;
+                    off[cnt][a] = s;
+                    ++cnt;
+                }
+        }
+        if (cnt == 0) continue;
+        uint32_t u[4];
+        draw(seed, rep, i, t, u);
+        uint32_t m = uniform_below(u[0], cnt);
+        for (uint32_t a = 0; a < d; ++a) coords[a][i] = wrap_add(c[a], off[m][a], sizes[a]);
+    }
+    return ORC_OK;
+}
