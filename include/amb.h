@@ -489,6 +489,36 @@ amb_status amb_view_destroy(amb_view *v);
 /* Wait for the table's stream; report device-side errors of view operations. */
 amb_status amb_table_synchronize(amb_table *t);
 
+/* Buffered per-agent writes (paper Sec. 3.2.1: per-agent record() calls are
+ * buffered and flushed by one id-keyed update per step).  A log belongs to a
+ * table (destroy it before the table).  amb_log_record appends k writes
+ * "column col of row ids[j] := values[j]" in order (values reduced to the
+ * column's type by two's-complement truncation; ids in [0, n), else
+ * AMB_EINVAL and nothing is appended); the log holds `capacity` writes.
+ * amb_log_flush applies every pending write so that, for each (row, column),
+ * the last recorded write wins, and empties the log (asynchronous). */
+typedef struct amb_log amb_log;
+amb_status amb_log_create(amb_table *t, uint32_t capacity, amb_log **out);
+amb_status amb_log_record(amb_log *l, int col, const int32_t *ids, const int64_t *values, size_t k, int on_device);
+amb_status amb_log_pending(amb_log *l, size_t *k);
+amb_status amb_log_flush(amb_log *l);
+amb_status amb_log_destroy(amb_log *l);
+
+/* Grid environments (paper Sec. 4.1): `steps` steps of a random walk on a
+ * d-dimensional lattice (d = 1..4; sizes[q] cells along axis q; positions in
+ * the int32 columns cols[0..d-1], each in [0, sizes[q])).  Each step every
+ * agent moves to a neighbour chosen uniformly, m = hi32(u0 * count) with u
+ * the agent's Philox draw for the step (key (seed, replicate), counter (id,
+ * step)), the m-th neighbour in this order: Moore (moore != 0): offsets in
+ * {-1, 0, 1}^d without zero, enumerated as base-3 numbers with axis 0 the
+ * fastest digit; von Neumann: (axis 0, -1), (axis 0, +1), (axis 1, -1), ...
+ * On a torus (torus != 0) coordinates wrap; otherwise only neighbours inside
+ * the box count, in the same order, and an agent with none stays.  d = 2,
+ * Moore, torus is the walk of amb_step.  Coordinates outside the box are left
+ * unchanged and reported by amb_table_synchronize. */
+amb_status amb_table_grid_walk(amb_table *t, const int *cols, uint32_t d, const uint32_t *sizes, int moore, int torus,
+                               uint64_t seed, uint32_t replicate, uint32_t step, uint32_t steps);
+
 /*
  * amb_cell_index without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate

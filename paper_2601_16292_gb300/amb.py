@@ -164,6 +164,13 @@ def lib():
             "amb_view_ids": (st, [vp, vp, sz, ctypes.c_int, ctypes.POINTER(sz)]),
             "amb_view_destroy": (st, [vp]),
             "amb_table_synchronize": (st, [vp]),
+            "amb_log_create": (st, [vp, u32, ctypes.POINTER(vp)]),
+            "amb_log_record": (st, [vp, ctypes.c_int, vp, vp, sz, ctypes.c_int]),
+            "amb_log_pending": (st, [vp, ctypes.POINTER(sz)]),
+            "amb_log_flush": (st, [vp]),
+            "amb_log_destroy": (st, [vp]),
+            "amb_table_grid_walk": (st, [vp, ctypes.POINTER(ctypes.c_int), u32, ctypes.POINTER(u32), ctypes.c_int,
+                                         ctypes.c_int, u64, u32, u32, u32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -686,6 +693,18 @@ class Table:
     def synchronize(self):
         _check(lib().amb_table_synchronize(self.handle))
 
+    def log(self, capacity):
+        """A buffered-write log of this table (Log)."""
+        return Log(self, capacity)
+
+    def grid_walk(self, cols, sizes, moore=True, torus=True, seed=0, rep=0, step=0, steps=1):
+        """`steps` grid-walk steps on the int32 coordinate columns `cols`."""
+        d = len(cols)
+        c = (ctypes.c_int * d)(*[self.col(x) for x in cols])
+        sz = (ctypes.c_uint32 * d)(*[int(v) for v in sizes])
+        _check(lib().amb_table_grid_walk(self.handle, c, d, sz, int(bool(moore)), int(bool(torus)), int(seed), int(rep),
+                                         int(step), int(steps)))
+
     def close(self):
         if self.handle is not None and self.handle.value:
             _check(lib().amb_table_destroy(self.handle))
@@ -772,3 +791,46 @@ class CPopulation(Population):
         out = torch.empty(self.n, dtype=dt, device=device)
         amb_read_column(self.handle, name, out)
         return out
+
+
+class Log:
+    """Buffered per-agent writes of a Table (amb_log): record, then flush once."""
+
+    def __init__(self, table, capacity):
+        self.table = table
+        h = ctypes.c_void_p()
+        _check(lib().amb_log_create(table.handle, int(capacity), ctypes.byref(h)))
+        self.handle = h
+
+    def record(self, name, ids, values):
+        if hasattr(ids, "data_ptr"):
+            pi, dev, k, _ = _buffer(ids)
+            pv, dev2, k2, _ = _buffer(values)
+            if dev != dev2 or k != k2:
+                raise ValueError("ids and values must have the same length and location")
+        else:
+            ids = np.ascontiguousarray(ids, dtype=np.int32)
+            values = np.ascontiguousarray(values, dtype=np.int64)
+            if ids.size != values.size:
+                raise ValueError("ids and values must have the same length")
+            pi, pv, k, dev = ctypes.c_void_p(ids.ctypes.data), ctypes.c_void_p(values.ctypes.data), ids.size, 0
+        _check(lib().amb_log_record(self.handle, self.table.col(name), pi, pv, k, dev))
+
+    def pending(self):
+        k = ctypes.c_size_t()
+        _check(lib().amb_log_pending(self.handle, ctypes.byref(k)))
+        return k.value
+
+    def flush(self):
+        _check(lib().amb_log_flush(self.handle))
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            _check(lib().amb_log_destroy(self.handle))
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

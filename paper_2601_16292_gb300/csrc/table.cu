@@ -36,6 +36,15 @@ struct amb_table {
     int live_views = 0;
 };
 
+struct amb_log {
+    amb_table *t = nullptr;
+    uint32_t capacity = 0, count = 0;
+    int32_t *ids = nullptr, *cols = nullptr;
+    int64_t *vals = nullptr;
+    std::vector<int32_t *> win;  // per column: the winning record per row (-1 = none), when used
+    std::vector<bool> used;      // columns recorded since the last flush
+};
+
 struct amb_view {
     amb_table *t = nullptr;
     int32_t *ids = nullptr;   // capacity entries
@@ -84,6 +93,7 @@ __device__ __forceinline__ bool compare(int64_t v, int64_t s)
 }
 
 constexpr int kMapNT = 256;
+constexpr int kMaxLogCols = 64;  // columns a buffered-write log can address
 
 // full-population view, scalar operand: 4 int32 (or 16 uint8) per 16-byte access
 template <int OP>
@@ -296,6 +306,127 @@ __global__ void fill_kernel(uint8_t *__restrict__ p, size_t bytes, uint32_t word
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nw; i += (size_t)gridDim.x * blockDim.x) w[i] = word;
 }
 
+// ------------------------------------------------------- buffered writes ---
+struct LogCols {
+    void *ptr[kMaxLogCols];
+    int32_t *win[kMaxLogCols];
+    uint8_t dtype[kMaxLogCols];
+};
+
+__global__ void log_claim_kernel(const int32_t *__restrict__ ids, const int32_t *__restrict__ cols, uint32_t k,
+                                 LogCols lc)
+{
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < k; e += gridDim.x * blockDim.x)
+        atomicMax(&lc.win[cols[e]][ids[e]], (int32_t)e);
+}
+
+__global__ void log_apply_kernel(const int32_t *__restrict__ ids, const int32_t *__restrict__ cols,
+                                 const int64_t *__restrict__ vals, uint32_t k, LogCols lc)
+{
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < k; e += gridDim.x * blockDim.x) {
+        const int32_t c = cols[e], id = ids[e];
+        if (lc.win[c][id] != (int32_t)e) continue;  // a later record of this row wins
+        if (lc.dtype[c] == AMB_DT_I32)
+            static_cast<int32_t *>(lc.ptr[c])[id] = (int32_t)(uint32_t)(uint64_t)vals[e];
+        else
+            static_cast<uint8_t *>(lc.ptr[c])[id] = (uint8_t)(uint64_t)vals[e];
+    }
+}
+
+__global__ void log_reset_kernel(const int32_t *__restrict__ ids, const int32_t *__restrict__ cols, uint32_t k,
+                                 LogCols lc)
+{
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < k; e += gridDim.x * blockDim.x)
+        lc.win[cols[e]][ids[e]] = -1;
+}
+
+__global__ void fill_i32_kernel(int32_t *__restrict__ p, uint32_t k, int32_t v)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) p[i] = v;
+}
+
+// ------------------------------------------------------------ grid walks ---
+struct GridWalkArgs {
+    int32_t *c[4];
+    uint32_t size[4];
+    uint32_t d, n, k0, k1, t0, steps;
+    int moore, torus;
+};
+
+__device__ __forceinline__ int32_t wrap_coord(int32_t v, int32_t o, uint32_t size)
+{
+    int64_t s = (int64_t)v + o;
+    if (s < 0) s += size;
+    if (s >= (int64_t)size) s -= size;
+    return (int32_t)s;
+}
+
+__global__ void grid_walk_kernel(GridWalkArgs a, uint32_t *err)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+        int32_t c[4] = {0, 0, 0, 0};
+        bool ok = true;
+        for (uint32_t q = 0; q < a.d; ++q) {
+            c[q] = a.c[q][i];
+            ok &= c[q] >= 0 && (uint32_t)c[q] < a.size[q];
+        }
+        if (!ok) {
+            atomicOr(err, ERR_RANGE);
+            continue;
+        }
+        for (uint32_t j = 0; j < a.steps; ++j) {
+            const U4 u = philox(i, a.t0 + j, a.k0, a.k1);
+            int32_t off[4] = {0, 0, 0, 0};
+            if (a.moore) {
+                // per dimension the admissible offsets (-1 if inside, 0, +1 if inside), in order
+                uint32_t v[4], lo[4], total = 1, center = 0, stride = 1;
+                for (uint32_t q = 0; q < a.d; ++q) {
+                    const bool dn = a.torus || c[q] > 0, up = a.torus || (uint32_t)c[q] + 1u < a.size[q];
+                    lo[q] = dn ? 1u : 0u;  // index of the zero offset in this dimension's list
+                    v[q] = 1u + (dn ? 1u : 0u) + (up ? 1u : 0u);
+                    center += lo[q] * stride;
+                    stride *= v[q];
+                    total *= v[q];
+                }
+                const uint32_t cnt = total - 1u;
+                if (cnt == 0) continue;
+                uint32_t m = below(u.w0, cnt);
+                if (m >= center) ++m;  // skip the zero offset
+                for (uint32_t q = 0; q < a.d; ++q) {
+                    off[q] = (int32_t)(m % v[q]) - (int32_t)lo[q];
+                    m /= v[q];
+                }
+            } else {
+                uint32_t cnt = 0;
+                for (uint32_t q = 0; q < a.d; ++q) {
+                    cnt += (a.torus || c[q] > 0) ? 1u : 0u;
+                    cnt += (a.torus || (uint32_t)c[q] + 1u < a.size[q]) ? 1u : 0u;
+                }
+                if (cnt == 0) continue;
+                uint32_t m = below(u.w0, cnt);
+                for (uint32_t q = 0; q < a.d; ++q) {
+                    if (a.torus || c[q] > 0) {
+                        if (m == 0) {
+                            off[q] = -1;
+                            break;
+                        }
+                        --m;
+                    }
+                    if (a.torus || (uint32_t)c[q] + 1u < a.size[q]) {
+                        if (m == 0) {
+                            off[q] = 1;
+                            break;
+                        }
+                        --m;
+                    }
+                }
+            }
+            for (uint32_t q = 0; q < a.d; ++q) c[q] = wrap_coord(c[q], off[q], a.size[q]);
+        }
+        for (uint32_t q = 0; q < a.d; ++q) a.c[q][i] = c[q];
+    }
+}
+
 unsigned map_grid(uint64_t work)
 {
     return grid_for(work, kMapNT, 152u * 16u);
@@ -433,7 +564,12 @@ amb_status table_error(amb_table *t)
     AMB_TRY_CUDA(cudaMemcpyAsync(&h, t->err, sizeof(h), cudaMemcpyDeviceToHost, t->stream));
     AMB_TRY_CUDA(cudaStreamSynchronize(t->stream));
     if (h & ERR_TIMEOUT) return fail(AMB_ETIMEOUT, "a bounded device-side wait ran out (error word 0x%x)", h);
-    if (h & ERR_RANGE) return fail(AMB_EINVAL, "an id outside [0, n) was given (error word 0x%x)", h);
+    if (h & ERR_RANGE) {
+        // caller input (ids, coordinates) out of range: reported once, the table stays usable
+        AMB_TRY_CUDA(cudaMemsetAsync(t->err, 0, sizeof(uint32_t), t->stream));
+        AMB_TRY_CUDA(cudaStreamSynchronize(t->stream));
+        return fail(AMB_EINVAL, "an id or coordinate outside its range was given (error word 0x%x)", h);
+    }
     if (h) return fail(AMB_EINVARIANT, "device error word 0x%x", h);
     return AMB_OK;
 }
@@ -743,6 +879,142 @@ amb_status amb_table_synchronize(amb_table *t)
 {
     if (!t) return fail(AMB_EINVAL, "null table");
     return table_error(t);
+}
+
+amb_status amb_log_create(amb_table *t, uint32_t capacity, amb_log **out)
+{
+    if (!t || !out) return fail(AMB_EINVAL, "null pointer");
+    *out = nullptr;
+    if (capacity > 0x7FFFFFFFu) return fail(AMB_EINVAL, "capacity must be < 2^31");
+    amb_log *l = new (std::nothrow) amb_log();
+    if (!l) return fail(AMB_ENOMEM, "host allocation failed");
+    l->t = t;
+    l->capacity = capacity;
+    amb_status st = dalloc(&l->ids, capacity, t->stream);
+    if (st == AMB_OK) st = dalloc(&l->cols, capacity, t->stream);
+    if (st == AMB_OK) st = dalloc(&l->vals, capacity, t->stream);
+    if (st != AMB_OK) {
+        dfree(l->ids, t->stream);
+        dfree(l->cols, t->stream);
+        dfree(l->vals, t->stream);
+        delete l;
+        return st;
+    }
+    t->live_views += 1;
+    *out = l;
+    return AMB_OK;
+}
+
+amb_status amb_log_record(amb_log *l, int col, const int32_t *ids, const int64_t *values, size_t k, int on_device)
+{
+    if (!l || ((!ids || !values) && k)) return fail(AMB_EINVAL, "null pointer");
+    amb_table *t = l->t;
+    Column *c = nullptr;
+    AMB_TRY(get_col(t, col, &c));
+    if (col >= kMaxLogCols) return fail(AMB_EINVAL, "a log addresses the first %d columns only", kMaxLogCols);
+    if (k > (size_t)(l->capacity - l->count)) return fail(AMB_EINVAL, "log full (%u of %u records)", l->count, l->capacity);
+    if (k == 0) return AMB_OK;
+    if (!on_device)
+        for (size_t i = 0; i < k; ++i)
+            if (ids[i] < 0 || (uint32_t)ids[i] >= t->n) return fail(AMB_EINVAL, "id %d at %zu outside [0, %u)", ids[i], i, t->n);
+    cudaStream_t s = t->stream;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    AMB_TRY_CUDA(cudaMemcpyAsync(l->ids + l->count, ids, k * sizeof(int32_t), kind, s));
+    AMB_TRY_CUDA(cudaMemcpyAsync(l->vals + l->count, values, k * sizeof(int64_t), kind, s));
+    fill_i32_kernel<<<grid_for(k, 256, 152u * 8u), 256, 0, s>>>(l->cols + l->count, (uint32_t)k, col);
+    AMB_TRY_CUDA(cudaGetLastError());
+    if (on_device) {
+        ids_check_kernel<<<grid_for(k, 256, 152u * 8u), 256, 0, s>>>(l->ids + l->count, (uint32_t)k, t->n, t->err);
+        AMB_TRY_CUDA(cudaGetLastError());
+        AMB_TRY(table_error(t));  // a bad id leaves the log unchanged (count not advanced)
+    } else {
+        AMB_TRY_CUDA(cudaStreamSynchronize(s));  // the caller may reuse its buffers
+    }
+    if (l->used.size() < t->cols.size()) l->used.resize(t->cols.size(), false);
+    l->used[(size_t)col] = true;
+    l->count += (uint32_t)k;
+    return AMB_OK;
+}
+
+amb_status amb_log_pending(amb_log *l, size_t *k)
+{
+    if (!l || !k) return fail(AMB_EINVAL, "null pointer");
+    *k = l->count;
+    return AMB_OK;
+}
+
+amb_status amb_log_flush(amb_log *l)
+{
+    if (!l) return fail(AMB_EINVAL, "null log");
+    amb_table *t = l->t;
+    cudaStream_t s = t->stream;
+    if (l->count == 0) return AMB_OK;
+    if (l->win.size() < t->cols.size()) l->win.resize(t->cols.size(), nullptr);
+    LogCols lc;
+    memset(&lc, 0, sizeof(lc));
+    for (size_t c = 0; c < t->cols.size() && c < (size_t)kMaxLogCols; ++c) {
+        lc.ptr[c] = t->cols[c].ptr;
+        lc.dtype[c] = (uint8_t)t->cols[c].dtype;
+        if (c < l->used.size() && l->used[c] && !l->win[c]) {
+            AMB_TRY(dalloc(&l->win[c], t->n, s));
+            AMB_TRY_CUDA(cudaMemsetAsync(l->win[c], 0xFF, (size_t)t->n * sizeof(int32_t), s));  // -1
+        }
+        lc.win[c] = l->win[c];
+    }
+    const unsigned g = grid_for(l->count, 256, 152u * 16u);
+    log_claim_kernel<<<g, 256, 0, s>>>(l->ids, l->cols, l->count, lc);
+    log_apply_kernel<<<g, 256, 0, s>>>(l->ids, l->cols, l->vals, l->count, lc);
+    log_reset_kernel<<<g, 256, 0, s>>>(l->ids, l->cols, l->count, lc);
+    AMB_TRY_CUDA(cudaGetLastError());
+    l->count = 0;
+    std::fill(l->used.begin(), l->used.end(), false);
+    return AMB_OK;
+}
+
+amb_status amb_log_destroy(amb_log *l)
+{
+    if (!l) return AMB_OK;
+    cudaStream_t s = l->t->stream;
+    dfree(l->ids, s);
+    dfree(l->cols, s);
+    dfree(l->vals, s);
+    for (int32_t *w : l->win) dfree(w, s);
+    l->t->live_views -= 1;
+    delete l;
+    return AMB_OK;
+}
+
+amb_status amb_table_grid_walk(amb_table *t, const int *cols, uint32_t d, const uint32_t *sizes, int moore, int torus,
+                               uint64_t seed, uint32_t replicate, uint32_t step, uint32_t steps)
+{
+    if (!t || !cols || !sizes) return fail(AMB_EINVAL, "null pointer");
+    if (d < 1 || d > 4) return fail(AMB_EINVAL, "grids have 1 to 4 dimensions");
+    if (seed > 0xFFFFFFFFull) return fail(AMB_EINVAL, "seed must be < 2^32");
+    if ((uint64_t)step + steps >= 0xFFFFFFFFull) return fail(AMB_EINVAL, "step index would reach 2^32 - 1");
+    GridWalkArgs a;
+    memset(&a, 0, sizeof(a));
+    for (uint32_t q = 0; q < d; ++q) {
+        Column *c = nullptr;
+        AMB_TRY(get_col(t, cols[q], &c));
+        if (c->dtype != AMB_DT_I32) return fail(AMB_EINVAL, "grid coordinates are int32 columns");
+        if (sizes[q] < 1 || sizes[q] > 0x7FFFFFFFu) return fail(AMB_EINVAL, "grid sizes must be in [1, 2^31)");
+        for (uint32_t r = 0; r < q; ++r)
+            if (cols[r] == cols[q]) return fail(AMB_EINVAL, "a column appears twice");
+        a.c[q] = static_cast<int32_t *>(c->ptr);
+        a.size[q] = sizes[q];
+    }
+    if (t->n == 0 || steps == 0) return AMB_OK;
+    a.d = d;
+    a.n = t->n;
+    a.k0 = (uint32_t)seed;
+    a.k1 = replicate;
+    a.t0 = step;
+    a.steps = steps;
+    a.moore = moore != 0;
+    a.torus = torus != 0;
+    grid_walk_kernel<<<grid_for(t->n, 256, 152u * 32u), 256, 0, t->stream>>>(a, t->err);
+    AMB_TRY_CUDA(cudaGetLastError());
+    return AMB_OK;
 }
 
 }  // extern "C"
