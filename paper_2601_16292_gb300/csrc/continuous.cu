@@ -45,12 +45,13 @@ __device__ __forceinline__ void cmove(float w, float h, float s, const U4 &u, fl
 
 struct Grid {
     float size;       // cell edge
+    float inv;        // 1 / size: cell lookups multiply (monotone; the margin in size absorbs the rounding)
     uint32_t gx, gy;  // cells per axis
 };
 
-__device__ __forceinline__ uint32_t cell_coord(float v, float size, uint32_t g)
+__device__ __forceinline__ uint32_t cell_coord(float v, float inv, uint32_t g)
 {
-    const float q = floorf(__fdiv_rn(v, size));
+    const float q = floorf(__fmul_rn(v, inv));
     const uint32_t c = q <= 0.0f ? 0u : (uint32_t)q;
     return c < g ? c : g - 1u;
 }
@@ -100,7 +101,7 @@ __global__ void csir_move_kernel(float *__restrict__ x, float *__restrict__ y, c
             y[i] = yi;
         }
         if (state[i] == AMB_I) {
-            const uint32_t c = cell_coord(yi, g.size, g.gy) * g.gx + cell_coord(xi, g.size, g.gx);
+            const uint32_t c = cell_coord(yi, g.inv, g.gy) * g.gx + cell_coord(xi, g.inv, g.gx);
             cell[i] = (int32_t)c;
             atomicAdd(&cnt[c], 1);
         }
@@ -132,7 +133,7 @@ __global__ void csir_contact_kernel(const float *__restrict__ x, const float *__
         uint32_t st = state[j];
         if (st == AMB_S) {
             const float xj = x[j], yj = y[j];
-            const uint32_t cx = cell_coord(xj, g.size, g.gx), cy = cell_coord(yj, g.size, g.gy);
+            const uint32_t cx = cell_coord(xj, g.inv, g.gx), cy = cell_coord(yj, g.inv, g.gy);
             uint32_t k = 0;
             const uint32_t y0 = cy ? cy - 1u : 0u, y1 = min(cy + 1u, g.gy - 1u);
             const uint32_t x0 = cx ? cx - 1u : 0u, x1 = min(cx + 1u, g.gx - 1u);
@@ -182,6 +183,145 @@ __global__ void csir_contact_kernel(const float *__restrict__ x, const float *__
     }
 }
 
+// Small populations: one CTA runs all k steps with positions, per-cell counts
+// and the infected agents' positions in shared memory (the same arithmetic as
+// the four-launch path; no launch per step).
+constexpr int kSmallNT = 1024;
+constexpr uint32_t kSmallMaxN = 8192;
+constexpr uint32_t kSmallMaxCells = 4096;
+
+__global__ void __launch_bounds__(kSmallNT) csir_small_kernel(float *__restrict__ gx_, float *__restrict__ gy_,
+                                                              uint8_t *__restrict__ state, int32_t *__restrict__ days,
+                                                              uint32_t n, float w, float h, float s, Grid g, float r2,
+                                                              uint32_t k0, uint32_t k1, uint32_t t0, uint32_t k,
+                                                              const uint32_t *__restrict__ t_inf, uint32_t K,
+                                                              uint32_t rec_steps, int64_t *__restrict__ rows)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *x = reinterpret_cast<float *>(smem_raw);
+    float *y = x + kSmallMaxN;
+    float2 *inf = reinterpret_cast<float2 *>(y + kSmallMaxN);
+    int32_t *start = reinterpret_cast<int32_t *>(inf + kSmallMaxN);  // kSmallMaxCells + 1
+    int32_t *cursor = start + kSmallMaxCells + 1;                     // kSmallMaxCells
+    __shared__ uint32_t s_warp[kSmallNT / 32 + 1];
+    __shared__ unsigned long long s_cnt[4];
+    const uint32_t tid = threadIdx.x, C = g.gx * g.gy;
+    for (uint32_t i = tid; i < n; i += kSmallNT) {
+        x[i] = gx_[i];
+        y[i] = gy_[i];
+    }
+    for (uint32_t j = 0; j < k; ++j) {
+        const uint32_t t = t0 + j;
+        for (uint32_t c = tid; c < C; c += kSmallNT) cursor[c] = 0;
+        if (tid < 4) s_cnt[tid] = 0ull;
+        __syncthreads();
+        // moves; start-of-step infected agents per cell
+        for (uint32_t i = tid; i < n; i += kSmallNT) {
+            float xi = x[i], yi = y[i];
+            if (s > 0.0f) {
+                cmove(w, h, s, philox(i, t, k0, k1), xi, yi);
+                x[i] = xi;
+                y[i] = yi;
+            }
+            if (state[i] == AMB_I)
+                atomicAdd(&cursor[cell_coord(yi, g.inv, g.gy) * g.gx + cell_coord(xi, g.inv, g.gx)], 1);
+        }
+        __syncthreads();
+        // exclusive scan of the counts: four cells per thread
+        {
+            uint32_t c4[4], sum = 0;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const uint32_t c = tid * 4u + (uint32_t)e;
+                c4[e] = c < C ? (uint32_t)cursor[c] : 0u;
+                sum += c4[e];
+            }
+            uint32_t total;
+            uint32_t off = block_exclusive_scan<kSmallNT>(sum, s_warp, &total);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const uint32_t c = tid * 4u + (uint32_t)e;
+                if (c < C) {
+                    start[c] = (int32_t)off;
+                    cursor[c] = (int32_t)off;
+                }
+                off += c4[e];
+            }
+            if (tid == 0) start[C] = (int32_t)total;
+        }
+        __syncthreads();
+        for (uint32_t i = tid; i < n; i += kSmallNT) {
+            if (state[i] != AMB_I) continue;
+            const float xi = x[i], yi = y[i];
+            const int32_t slot = atomicAdd(&cursor[cell_coord(yi, g.inv, g.gy) * g.gx + cell_coord(xi, g.inv, g.gx)], 1);
+            inf[slot] = make_float2(xi, yi);
+        }
+        __syncthreads();
+        // infection and recovery against the start-of-step infected set
+        uint32_t cs = 0, ci = 0, cr = 0, fresh = 0;
+        for (uint32_t i = tid; i < n; i += kSmallNT) {
+            uint32_t st = state[i];
+            if (st == AMB_S) {
+                const float xj = x[i], yj = y[i];
+                const uint32_t cx = cell_coord(xj, g.inv, g.gx), cy = cell_coord(yj, g.inv, g.gy);
+                const uint32_t ya = cy ? cy - 1u : 0u, yb = min(cy + 1u, g.gy - 1u);
+                const uint32_t xa = cx ? cx - 1u : 0u, xb = min(cx + 1u, g.gx - 1u);
+                uint32_t kk = 0;
+                for (uint32_t yy = ya; yy <= yb; ++yy) {
+                    const int32_t b = start[yy * g.gx + xa], e = start[yy * g.gx + xb + 1u];
+                    for (int32_t q = b; q < e; ++q) {
+                        const float2 p = inf[q];
+                        const float dx = __fsub_rn(p.x, xj), dy = __fsub_rn(p.y, yj);
+                        kk += (__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)) <= r2) ? 1u : 0u;
+                    }
+                }
+                if (kk) {
+                    const U4 u = philox(i, t, k0, k1);
+                    if (u.w2 < t_inf[kk < K ? kk : K]) {
+                        st = AMB_I;
+                        state[i] = (uint8_t)AMB_I;
+                        days[i] = 0;
+                        ++fresh;
+                    }
+                }
+            } else if (st == AMB_I) {
+                const int32_t d = days[i] + 1;
+                days[i] = d;
+                if ((uint32_t)d >= rec_steps) {
+                    st = AMB_R;
+                    state[i] = (uint8_t)AMB_R;
+                }
+            }
+            cs += (st == AMB_S);
+            ci += (st == AMB_I);
+            cr += (st == AMB_R);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cs += __shfl_down_sync(0xffffffffu, cs, o);
+            ci += __shfl_down_sync(0xffffffffu, ci, o);
+            cr += __shfl_down_sync(0xffffffffu, cr, o);
+            fresh += __shfl_down_sync(0xffffffffu, fresh, o);
+        }
+        if ((tid & 31u) == 0) {
+            if (cs) atomicAdd(&s_cnt[0], (unsigned long long)cs);
+            if (ci) atomicAdd(&s_cnt[1], (unsigned long long)ci);
+            if (cr) atomicAdd(&s_cnt[2], (unsigned long long)cr);
+            if (fresh) atomicAdd(&s_cnt[3], (unsigned long long)fresh);
+        }
+        __syncthreads();
+        if (tid < 4) rows[(size_t)j * 4u + tid] = (int64_t)s_cnt[tid];
+        __syncthreads();
+    }
+    for (uint32_t i = tid; i < n; i += kSmallNT) {
+        gx_[i] = x[i];
+        gy_[i] = y[i];
+    }
+}
+
+constexpr size_t kSmallSmem =
+    (size_t)kSmallMaxN * (4u + 4u + 8u) + ((size_t)kSmallMaxCells * 2u + 1u) * 4u;
+
 // coordinates outside the box (or NaN)
 __global__ void cbounds_kernel(const float *__restrict__ v, uint32_t n, float hi, unsigned long long *bad)
 {
@@ -213,6 +353,7 @@ Grid grid_of(const amb_cparams &p)
     if (!(size > 0.0f)) size = 1.0f;  // empty box: one cell
     Grid g;
     g.size = size;
+    g.inv = 1.0f / size;
     g.gx = (uint32_t)std::min(1024.0f, std::max(1.0f, std::ceil(p.width / size)));
     g.gy = (uint32_t)std::min(1024.0f, std::max(1.0f, std::ceil(p.height / size)));
     return g;
@@ -268,10 +409,22 @@ amb_status cont_steps(amb_pop *pop, uint32_t k)
         pop->launches += 1;
         return AMB_OK;
     }
-    AMB_TRY_CUDA(cudaMemsetAsync(rows, 0, (size_t)k * 4u * sizeof(int64_t), s));
     const Grid g = grid_of(p);
     const uint32_t C = g.gx * g.gy;
     const float r2 = p.radius * p.radius;
+    if (n <= kSmallMaxN && C <= kSmallMaxCells) {
+        // the whole run in one CTA (rows are written for every step)
+        AMB_TRY_CUDA(cudaFuncSetAttribute(csir_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)kSmallSmem));
+        csir_small_kernel<<<1, kSmallNT, kSmallSmem, s>>>(pop->fx, pop->fy, pop->state, pop->days, n, p.width,
+                                                           p.height, p.step, g, r2, pop->key0, pop->key1,
+                                                           (uint32_t)pop->t, k, pop->t_inf_d, pop->K,
+                                                           p.recovery_steps, rows);
+        AMB_TRY_CUDA(cudaGetLastError());
+        pop->launches += 1;
+        return AMB_OK;
+    }
+    AMB_TRY_CUDA(cudaMemsetAsync(rows, 0, (size_t)k * 4u * sizeof(int64_t), s));
     const unsigned grid = grid_for(n, 256, 152u * 16u);
     for (uint32_t j = 0; j < k; ++j) {
         const uint32_t t = (uint32_t)(pop->t + j);
