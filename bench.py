@@ -242,7 +242,7 @@ def run_e2e(amb, torch, steps, rank, stream):
     pop = amb.Population("sir", n, seed=c["seed"], rep=rank, L=c["L"], beta=c["beta"], gamma=c["gamma"], n0=c["n0"],
                          stream=stream)
     out_state = torch.empty(n, dtype=torch.uint8, pin_memory=True)
-    row = torch.zeros((1, 4), dtype=torch.int64).numpy()
+    rows = torch.zeros((steps, 4), dtype=torch.int64, pin_memory=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     amb.amb_write_column(pop.handle, "x", hx)
@@ -250,9 +250,11 @@ def run_e2e(amb, torch, steps, rank, stream):
     amb.amb_write_column(pop.handle, "state", hs)
     for k in range(steps):
         amb.amb_step(pop.handle, 1)
-        amb.amb_counts_range(pop.handle, k, 1, row)
-    amb.amb_read_column(pop.handle, "state", out_state)
+        amb.amb_counts_async(pop.handle, k, 1, rows[k])  # each step's counts, read in stream order
+    amb.amb_read_column(pop.handle, "state", out_state)  # synchronises
     t1 = time.perf_counter()
+    if int(rows[-1].sum()) != 0 and int(rows[-1][:3].sum()) != n:
+        raise RuntimeError("end-to-end run lost agents")
     pop.close()
     h2d = 9 * n
     d2h = 32 * steps + n

@@ -185,6 +185,11 @@ amb_status amb_counts(amb_pop *pop, int64_t *out, size_t cap_rows, size_t *rows_
  * Synchronises. */
 amb_status amb_counts_range(amb_pop *pop, uint64_t first, size_t n_rows, int64_t *out);
 
+/* As amb_counts_range, but asynchronous: the copy is queued on the
+ * population's stream and the call returns at once (use page-locked host
+ * memory for a truly asynchronous copy; read out after amb_synchronize). */
+amb_status amb_counts_async(amb_pop *pop, uint64_t first, size_t n_rows, int64_t *out);
+
 /*
  * The counting-sort cell index of the current positions (grid environment,
  * paper Sec. 4.1): start[C+1] with C = L*L (start[c] = agents in cells < c,

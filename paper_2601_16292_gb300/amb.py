@@ -118,6 +118,7 @@ def lib():
             "amb_counts": (st, [vp, vp, sz, ctypes.POINTER(sz)]),
             "amb_read_index": (st, [vp, vp, vp, ctypes.c_int]),
             "amb_counts_range": (st, [vp, u64, sz, vp]),
+            "amb_counts_async": (st, [vp, u64, sz, vp]),
             "amb_launch_count": (u64, [vp]),
             "amb_invariants": (st, [vp, ctypes.POINTER(amb_invariant_report)]),
             "amb_stats_compute": (st, [vp, ctypes.POINTER(amb_stats), vp, sz, ctypes.POINTER(sz)]),
@@ -260,6 +261,13 @@ def amb_counts_range(pop, first, n_rows, out=None):
         out = np.zeros((max(int(n_rows), 1), 4), dtype=np.int64)
     _check(lib().amb_counts_range(pop, int(first), int(n_rows), ctypes.c_void_p(out.ctypes.data)))
     return out[:int(n_rows)]
+
+
+def amb_counts_async(pop, first, n_rows, out):
+    """Queue a copy of count rows into `out` (pinned torch tensor or numpy
+    array of n_rows x 4 int64); read it after amb_synchronize."""
+    p, _, _, _ = _buffer(out)
+    _check(lib().amb_counts_async(pop, int(first), int(n_rows), p))
 
 
 def amb_launch_count(pop):

@@ -202,6 +202,7 @@ struct amb_pop {
     uint2 *rec[2] = {nullptr, nullptr};  // {id, word} per slot
     int32_t *row_start[2] = {nullptr, nullptr};
     int cur = 0;
+    bool band_dirty = false;  // x, y, state hold written columns; records rebuilt before use
     uint32_t band_rows = 0, n_bands = 0;
     uint32_t band_grid = 0;
     uint32_t *band_wide = nullptr;  // per-CTA 32-bit counters for bands too dense for 16-bit ones
@@ -231,6 +232,7 @@ struct amb_pop {
 };
 
 namespace amb {
+amb_status band_sync_records(amb_pop *pop);
 bool is_continuous(const amb_pop *pop);
 amb_status cont_steps(amb_pop *pop, uint32_t k);
 amb_status cont_read_column(amb_pop *pop, amb_col col, void *dst, size_t n, int dst_on_device);

@@ -46,6 +46,7 @@ amb_status advance(const std::vector<amb_pop *> &pops, const std::vector<uint32_
         amb_pop *p = pops[i];
         const uint32_t k = ks[i];
         if (p->t + k >= (uint64_t)kInitStep) return fail(AMB_EINVAL, "job %zu: too many steps", i);
+        AMB_TRY(band_sync_records(p));
         AMB_TRY(ensure_series(p, p->t + k));
         if (k) AMB_TRY_CUDA(cudaMemsetAsync(p->series + (size_t)p->t * 4u, 0, (size_t)k * 4u * sizeof(int64_t), s));
         if (p->model == AMB_SIR) {

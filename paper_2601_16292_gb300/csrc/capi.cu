@@ -195,6 +195,20 @@ static amb_status copy_out(const void *src_dev, void *dst, size_t bytes, int dst
 
 static bool uses_band(const amb_pop *pop) { return pop->model == AMB_SIR && pop->path == AMB_SIR_BAND; }
 
+// Band path after column writes: rebuild the cell-ordered records from the
+// staged id-ordered columns (once, however many columns were written).
+amb_status band_sync_records(amb_pop *pop)
+{
+    if (!uses_band(pop) || !pop->band_dirty) return AMB_OK;
+    cudaStream_t s = pop->stream;
+    const amb_status st = sir_band_init(pop, pop->x, pop->y, pop->state);
+    dfree(pop->x, s);
+    dfree(pop->y, s);
+    dfree(pop->state, s);
+    pop->band_dirty = false;
+    return st;
+}
+
 // Cell index of the current positions for the id-ordered layouts.
 static amb_status build_index(amb_pop *pop)
 {
@@ -450,6 +464,7 @@ amb_status amb_synchronize(amb_pop *pop)
 amb_status amb_step(amb_pop *pop, uint32_t k)
 {
     if (!pop) return fail(AMB_EINVAL, "null population");
+    AMB_TRY(band_sync_records(pop));
     if (k == 0) return AMB_OK;
     if (pop->t + k >= (uint64_t)kInitStep) return fail(AMB_EINVAL, "step counter would reach 2^32 - 1");
     AMB_TRY(ensure_series(pop, pop->t + k));
@@ -481,7 +496,9 @@ amb_status amb_set_step(amb_pop *pop, uint64_t t)
     pop->conservation_from = t;
     pop->monotone_from = t;
     amb_status st = AMB_OK;
-    if (uses_band(pop) && pop->p.n) {
+    if (uses_band(pop) && pop->band_dirty) {
+        st = band_sync_records(pop);  // the staged columns, with the draws of step t
+    } else if (uses_band(pop) && pop->p.n) {
         // the records carry each agent's draws for the next step: redraw them for step t
         const uint32_t n = pop->p.n;
         int32_t *x = nullptr, *y = nullptr;
@@ -550,20 +567,24 @@ amb_status amb_write_column(amb_pop *pop, amb_col col, const void *src, size_t n
             dfree(mm, s);
             dfree(sum, s);
         } else if (uses_band(pop)) {
-            // materialise id-ordered columns, replace one, rebuild the records
-            int32_t *x = nullptr, *y = nullptr;
-            uint8_t *state = nullptr;
-            if ((st = dalloc(&x, n, s)) == AMB_OK && (st = dalloc(&y, n, s)) == AMB_OK &&
-                (st = dalloc(&state, n, s)) == AMB_OK && (st = sir_band_read(pop, AMB_COL_X, x)) == AMB_OK &&
-                (st = sir_band_read(pop, AMB_COL_Y, y)) == AMB_OK &&
-                (st = sir_band_read(pop, AMB_COL_STATE, state)) == AMB_OK) {
-                void *dstc = (col == AMB_COL_X) ? (void *)x : (col == AMB_COL_Y) ? (void *)y : (void *)state;
-                cudaMemcpyAsync(dstc, tmp, n * esz, cudaMemcpyDeviceToDevice, s);
-                st = sir_band_init(pop, x, y, state);
+            // stage id-ordered columns (materialised from the records on the
+            // first write); the records are rebuilt once, before they are next used
+            if (!pop->band_dirty) {
+                if ((st = dalloc(&pop->x, n, s)) == AMB_OK && (st = dalloc(&pop->y, n, s)) == AMB_OK &&
+                    (st = dalloc(&pop->state, n, s)) == AMB_OK && (st = sir_band_read(pop, AMB_COL_X, pop->x)) == AMB_OK &&
+                    (st = sir_band_read(pop, AMB_COL_Y, pop->y)) == AMB_OK &&
+                    (st = sir_band_read(pop, AMB_COL_STATE, pop->state)) == AMB_OK) {
+                    pop->band_dirty = true;
+                } else {
+                    dfree(pop->x, s);
+                    dfree(pop->y, s);
+                    dfree(pop->state, s);
+                }
             }
-            dfree(x, s);
-            dfree(y, s);
-            dfree(state, s);
+            if (st == AMB_OK) {
+                void *dstc = (col == AMB_COL_X) ? (void *)pop->x : (col == AMB_COL_Y) ? (void *)pop->y : (void *)pop->state;
+                cudaMemcpyAsync(dstc, tmp, n * esz, cudaMemcpyDeviceToDevice, s);
+            }
             pop->monotone_from = pop->t;
         } else {
             void *dstc = (col == AMB_COL_X) ? (void *)pop->x : (col == AMB_COL_Y) ? (void *)pop->y : (void *)pop->state;
@@ -585,6 +606,7 @@ amb_status amb_write_column(amb_pop *pop, amb_col col, const void *src, size_t n
 amb_status amb_read_column(amb_pop *pop, amb_col col, void *dst, size_t n, int dst_on_device)
 {
     if (!pop || (!dst && n)) return fail(AMB_EINVAL, "null pointer");
+    AMB_TRY(band_sync_records(pop));
     if (n != pop->p.n) return fail(AMB_EINVAL, "column length %zu != n = %u", n, pop->p.n);
     if (is_continuous(pop)) {
         AMB_TRY(device_error(pop));
@@ -631,11 +653,23 @@ amb_status amb_counts_range(amb_pop *pop, uint64_t first, size_t n_rows, int64_t
     return copy_out(pop->series + first * 4u, out, n_rows * 4u * sizeof(int64_t), 0, pop->stream);
 }
 
+amb_status amb_counts_async(amb_pop *pop, uint64_t first, size_t n_rows, int64_t *out)
+{
+    if (!pop || (!out && n_rows)) return fail(AMB_EINVAL, "null pointer");
+    if (first + n_rows > pop->t) return fail(AMB_EINVAL, "rows %llu..%llu not recorded yet", (unsigned long long)first,
+                                             (unsigned long long)(first + n_rows));
+    if (n_rows)
+        AMB_TRY_CUDA(cudaMemcpyAsync(out, pop->series + first * 4u, n_rows * 4u * sizeof(int64_t), cudaMemcpyDefault,
+                                     pop->stream));
+    return AMB_OK;
+}
+
 uint64_t amb_launch_count(const amb_pop *pop) { return pop ? pop->launches : 0; }
 
 amb_status amb_read_index(amb_pop *pop, int32_t *start, int32_t *ids, int dst_on_device)
 {
     if (!pop || !start || (!ids && pop->p.n)) return fail(AMB_EINVAL, "null pointer");
+    AMB_TRY(band_sync_records(pop));
     if (pop->model == AMB_WEALTH || is_continuous(pop)) return fail(AMB_EINVAL, "this model has no integer grid");
     const uint64_t C = (uint64_t)pop->p.grid_side * pop->p.grid_side;
     if (C >= 0x80000000ull) return fail(AMB_EINVAL, "index needs L*L < 2^31");
@@ -661,6 +695,7 @@ amb_status amb_read_index(amb_pop *pop, int32_t *start, int32_t *ids, int dst_on
 amb_status amb_occupancy(amb_pop *pop, int32_t *occ, int dst_on_device)
 {
     if (!pop || !occ) return fail(AMB_EINVAL, "null pointer");
+    AMB_TRY(band_sync_records(pop));
     if (pop->model == AMB_WEALTH) return fail(AMB_EINVAL, "the wealth model has no grid");
     const uint64_t C = (uint64_t)pop->p.grid_side * pop->p.grid_side;
     if (C >= 0x80000000ull) return fail(AMB_EINVAL, "occupancy needs L*L < 2^31");
@@ -678,6 +713,7 @@ amb_status amb_occupancy(amb_pop *pop, int32_t *occ, int dst_on_device)
 amb_status amb_invariants(amb_pop *pop, amb_invariant_report *out)
 {
     if (!pop || !out) return fail(AMB_EINVAL, "null pointer");
+    AMB_TRY(band_sync_records(pop));
     AMB_TRY(device_error(pop));
     amb_invariant_report r;
     r.ok = 1;
@@ -757,6 +793,7 @@ amb_status amb_invariants(amb_pop *pop, amb_invariant_report *out)
 amb_status amb_stats_compute(amb_pop *pop, amb_stats *out, int64_t *hist, size_t hist_cap, size_t *hist_len)
 {
     if (!pop || !out) return fail(AMB_EINVAL, "null pointer");
+    AMB_TRY(band_sync_records(pop));
     AMB_TRY(device_error(pop));
     amb_stats r;
     memset(&r, 0, sizeof(r));

@@ -312,7 +312,7 @@ __device__ __forceinline__ uint32_t new_state(const BandArgs &a, const Ctr &ctr,
     } else if (st == AMB_I) {
         if ((w >> kAuxRecShift) & 1u) st = AMB_R;
     }
-    tl.s += (st == AMB_S);
+    tl.s += 1u;
     tl.i += (st == AMB_I);
     tl.r += (st == AMB_R);
     return st;
@@ -589,6 +589,7 @@ __device__ __forceinline__ void flush_tally(BandShared &sh, Tally &tl, int64_t *
         tl.fresh += __shfl_down_sync(0xffffffffu, tl.fresh, o);
     }
     if ((tid & 31u) == 0) {
+        tl.s -= tl.i + tl.r;
         if (tl.s) atomicAdd(&sh.cnt[0], (unsigned long long)tl.s);
         if (tl.i) atomicAdd(&sh.cnt[1], (unsigned long long)tl.i);
         if (tl.r) atomicAdd(&sh.cnt[2], (unsigned long long)tl.r);

@@ -72,3 +72,47 @@ def test_bounded_wait_times_out_and_device_stays_usable(stream):
     p.step(5)
     assert p.invariants()["ok"]
     p.close()
+
+
+def test_written_columns_read_back_and_step_once_rebuilt(stream):
+    """Band path: several column writes are staged and the records rebuilt
+    once; reads see the written values, and stepping equals a population
+    given the same columns by one rebuild per write (the earlier behaviour is
+    equivalent to rebuilding after every write)."""
+    n, L = 20_000, 150
+    rng = np.random.default_rng(4)
+    x = rng.integers(0, L, n).astype(np.int32)
+    y = rng.integers(0, L, n).astype(np.int32)
+    s = rng.integers(0, 3, n).astype(np.uint8)
+    a = amb.Population("sir", n, seed=3, L=L, beta=0.3, gamma=0.05, n0=10, stream=stream)
+    a.write("x", x)
+    a.write("y", y)
+    a.write("state", s)
+    assert np.array_equal(a.column("x").cpu().numpy(), x)
+    assert np.array_equal(a.column("state").cpu().numpy(), s)
+    b = amb.Population("sir", n, seed=3, L=L, beta=0.3, gamma=0.05, n0=10, stream=stream)
+    b.write("x", x)
+    b.column("x")  # forces a rebuild between the writes
+    b.write("y", y)
+    b.column("y")
+    b.write("state", s)
+    a.step(12)
+    b.step(12)
+    for c in ("x", "y", "state"):
+        assert torch.equal(a.column(c), b.column(c)), c
+    assert np.array_equal(a.counts(), b.counts())
+    a.close()
+    b.close()
+
+
+def test_async_counts_equal_counts(stream):
+    p = amb.Population("sir", 50_000, seed=9, L=290, beta=0.2, gamma=0.05, n0=50, stream=stream)
+    rows = torch.zeros((20, 4), dtype=torch.int64, pin_memory=True)
+    for k in range(20):
+        p.step(1)
+        amb.amb_counts_async(p.handle, k, 1, rows[k])
+    p.synchronize()
+    assert np.array_equal(rows.numpy(), p.counts())
+    with pytest.raises(amb.AmbError):
+        amb.amb_counts_async(p.handle, 20, 1, rows[0])
+    p.close()
