@@ -148,9 +148,11 @@ __global__ void __launch_bounds__(kMapNT) map_col_kernel(D *__restrict__ d, cons
 }
 
 // ---------------------------------------------------------------- where ---
-constexpr int kWhereNT = 256;
-constexpr int kWhereItems = 16;                       // per thread
-constexpr uint32_t kWhereTile = kWhereNT * kWhereItems;  // 4096 ids per tile
+constexpr int kWhereNT = 512;
+constexpr int kWhereItems = 32;                          // per thread
+constexpr uint32_t kWhereTile = kWhereNT * kWhereItems;  // ids per tile
+constexpr int kWhereCtasPerSm = 3;                       // the staged ids take 64 KiB of shared memory per CTA
+static_assert(kWhereItems % 16 == 0 && kWhereItems <= 32, "predicate bits of a thread fit one word");
 
 template <int CMP, class T>
 __global__ void __launch_bounds__(kWhereNT) where_kernel(const T *__restrict__ c, uint32_t n, int64_t s,
@@ -161,7 +163,7 @@ __global__ void __launch_bounds__(kWhereNT) where_kernel(const T *__restrict__ c
 {
     __shared__ uint32_t s_tile, s_prefix;
     __shared__ uint32_t s_warp[kWhereNT / 32 + 1];
-    __shared__ int32_t s_ids[kWhereTile];
+    extern __shared__ int32_t s_ids[];  // kWhereTile (dynamic: the tile's ids in order)
     const uint32_t tid = threadIdx.x;
     if (blockIdx.x == 0 && tid == 0) tickets[parity ^ 1u] = 0ull;
     for (;;) {
@@ -183,10 +185,14 @@ __global__ void __launch_bounds__(kWhereNT) where_kernel(const T *__restrict__ c
                     bits |= (uint32_t)compare<CMP>(v.w, s) << (4 * q + 3);
                 }
             } else {
-                const uint4 v = *reinterpret_cast<const uint4 *>(c + i0);
-                const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                for (int k = 0; k < 16; ++k) bits |= (uint32_t)compare<CMP>((w[k >> 2] >> (8 * (k & 3))) & 0xFFu, s) << k;
+                for (int q = 0; q < kWhereItems / 16; ++q) {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(c + i0 + 16 * q);
+                    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int k = 0; k < 16; ++k)
+                        bits |= (uint32_t)compare<CMP>((w[k >> 2] >> (8 * (k & 3))) & 0xFFu, s) << (16 * q + k);
+                }
             }
         } else {
             for (uint32_t k = 0; k < (uint32_t)kWhereItems; ++k)
@@ -499,11 +505,13 @@ amb_status launch_where_t(amb_table *t, const T *c, int cmp, int64_t s, amb_view
     AMB_TRY(t->lb.ensure(n_tiles, st));
     uint32_t parity, epoch;
     t->lb.next(&parity, &epoch);
-    const unsigned g = std::min<uint32_t>(n_tiles, 152u * 8u);
-#define WHERE_CASE(C)                                                                                           \
-    case C:                                                                                                     \
-        where_kernel<C, T><<<g, kWhereNT, 0, st>>>(c, n, s, v->ids, v->count, n_tiles, t->lb.tickets, parity, \
-                                                   t->lb.status, epoch, t->err);                                \
+    const unsigned g = std::min<uint32_t>(n_tiles, 152u * kWhereCtasPerSm);
+    constexpr size_t smem = (size_t)kWhereTile * sizeof(int32_t);
+#define WHERE_CASE(C)                                                                                              \
+    case C:                                                                                                        \
+        AMB_TRY_CUDA(cudaFuncSetAttribute(where_kernel<C, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+        where_kernel<C, T><<<g, kWhereNT, smem, st>>>(c, n, s, v->ids, v->count, n_tiles, t->lb.tickets, parity,     \
+                                                      t->lb.status, epoch, t->err);                                 \
         break;
     switch (cmp) {
         WHERE_CASE(AMB_CMP_EQ)

@@ -13,7 +13,7 @@ from paper_2601_16292_gb300 import amb
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-SIZES = [0, 1, 5, 17, 4095, 4096, 4099, 3 * 4096 + 13, (1 << 20) + 7]
+SIZES = [0, 1, 5, 17, 4095, 4099, 16383, 16384, 16385, 3 * 16384 + 13, (1 << 20) + 7]
 RNG = np.random.default_rng(11)
 
 
