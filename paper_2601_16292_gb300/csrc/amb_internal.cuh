@@ -206,8 +206,6 @@ struct amb_pop {
     uint32_t band_rows = 0, n_bands = 0;
     uint32_t band_grid = 0;
     uint32_t *band_wide = nullptr;  // per-CTA 32-bit counters for bands too dense for 16-bit ones
-    uint32_t stage_cap = 0;         // agents the shared-memory stage of a band holds
-    uint32_t stage_off = 0;         // its word offset in the step kernel's dynamic shared memory
     uint32_t band_smem = 0;         // dynamic shared memory of the step kernel (bytes)
 
     // SIR thresholds
