@@ -275,6 +275,15 @@ def sweep_bench(amb, torch, stream, rank, world):
     ms = b.run(autotune=True)
     wall = time.perf_counter() - t0
     info = b.info()
+    # algorithmic bytes of the run: SIR 18 + 8 + 8 C/N per agent-step; wealth
+    # 8 per agent-step (read and write w) + 8 per donor (the recipient's
+    # read-modify-write), donors taken from each job's own count rows
+    alg = 0.0
+    for i, j in enumerate(jobs):
+        if j["model"] == "sir":
+            alg += j["steps"] * (26.0 * j["n"] + 8.0 * j["L"] * j["L"])
+        else:
+            alg += j["steps"] * 8.0 * j["n"] + 8.0 * float(b.population(i).counts()[:, 0].sum())
     b.close()
     # one job at a time: create, step all its steps, read its counts, destroy
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -296,7 +305,8 @@ def sweep_bench(amb, torch, stream, rank, world):
     wall_one = time.perf_counter() - t1
     return {"jobs": len(jobs), "agent_steps": total,
             "batched": {"value": total / (ms / 1e3), "device_ms": ms, "wall_s": wall, "launches": info["launches"],
-                        "band_rows_cap": info["band_rows_cap"], "spread_bands": info["spread_bands"]},
+                        "band_rows_cap": info["band_rows_cap"], "spread_bands": info["spread_bands"],
+                        "algorithmic_gbs": alg / (ms / 1e3) / 1e9, "hbm_frac": alg / (ms / 1e3) / 1e9 / load_peaks()[0]},
             "one_at_a_time": {"value": total / (dev_ms / 1e3), "device_ms": dev_ms, "wall_s": wall_one,
                               "wall_value": total / wall_one, "launches": launches},
             "speedup_device": dev_ms / ms, "unit": "agent-steps/s"}
