@@ -45,7 +45,8 @@ typedef enum {
     AMB_ETIMEOUT = 5,    /* a bounded device-side wait ran out; results invalid */
     AMB_EBUSY = 6,       /* server: job not finished yet */
     AMB_EBUDGET = 7,     /* server: job can never fit in the HBM budget */
-    AMB_ENOTFOUND = 8    /* server: unknown ticket */
+    AMB_ENOTFOUND = 8,   /* server: unknown ticket */
+    AMB_ECANCELED = 9    /* server: the job was cancelled */
 } amb_status;
 
 typedef enum {
@@ -372,7 +373,7 @@ typedef struct {
 } amb_result;
 
 typedef struct {
-    uint64_t submitted, admitted, completed, failed;
+    uint64_t submitted, admitted, completed, failed, cancelled;
     uint64_t agent_steps;  /* of completed jobs */
     uint64_t iterations, launches;
     size_t hbm_in_use, hbm_peak; /* by amb_job_bytes accounting */
@@ -406,6 +407,11 @@ amb_status amb_server_counts(amb_server *s, uint64_t ticket, int64_t *out, size_
 /* A kept final column of a finished job, in id order, into host memory dst
  * (n = the job's n elements; int32, or uint8 for the state). */
 amb_status amb_server_read_column(amb_server *s, uint64_t ticket, amb_col col, void *dst, size_t n);
+
+/* Cancel a job: a queued job ends at once, a running one after the current
+ * iteration (its device memory is freed then); its result reports
+ * AMB_ECANCELED.  A finished job is left as it is. */
+amb_status amb_server_cancel(amb_server *s, uint64_t ticket);
 
 /* Forget a finished job's result (its ticket becomes unknown). */
 amb_status amb_server_release(amb_server *s, uint64_t ticket);
@@ -554,6 +560,12 @@ amb_status amb_cell_index_noalloc(const int32_t *x, const int32_t *y, uint32_t n
  * outcome, with *waited_s the time waited, and the device stays usable.  Any
  * other status means the bound did not work. */
 amb_status amb_selfcheck_wait_timeout(void *cuda_stream, double *waited_s);
+
+/* Fault-injection hook for tests (no counterpart in the paper): the next k
+ * population creations (amb_create, amb_create_continuous, batch and server
+ * admissions included) fail with AMB_ENOMEM before touching the device.
+ * k = 0 turns it off.  Process-wide. */
+amb_status amb_debug_fail_creates(uint32_t k);
 
 /* Version string of the library build. */
 const char *amb_version(void);

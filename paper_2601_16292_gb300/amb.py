@@ -15,9 +15,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libamb.so")
 
 AMB_OK, AMB_EINVAL, AMB_ENOMEM, AMB_ECUDA, AMB_EINVARIANT = 0, 1, 2, 3, 4
-AMB_ETIMEOUT, AMB_EBUSY, AMB_EBUDGET, AMB_ENOTFOUND = 5, 6, 7, 8
+AMB_ETIMEOUT, AMB_EBUSY, AMB_EBUDGET, AMB_ENOTFOUND, AMB_ECANCELED = 5, 6, 7, 8, 9
 STATUS_NAMES = {0: "AMB_OK", 1: "AMB_EINVAL", 2: "AMB_ENOMEM", 3: "AMB_ECUDA", 4: "AMB_EINVARIANT",
-                5: "AMB_ETIMEOUT", 6: "AMB_EBUSY", 7: "AMB_EBUDGET", 8: "AMB_ENOTFOUND"}
+                5: "AMB_ETIMEOUT", 6: "AMB_EBUSY", 7: "AMB_EBUDGET", 8: "AMB_ENOTFOUND", 9: "AMB_ECANCELED"}
 
 AMB_WEALTH, AMB_WALK, AMB_SIR, AMB_CWALK, AMB_CSIR = 0, 1, 2, 3, 4
 MODELS = {"wealth": AMB_WEALTH, "walk": AMB_WALK, "sir": AMB_SIR, "cwalk": AMB_CWALK, "csir": AMB_CSIR}
@@ -88,7 +88,7 @@ class amb_result(ctypes.Structure):
 
 class amb_server_report(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
-                ("failed", ctypes.c_uint64), ("agent_steps", ctypes.c_uint64), ("iterations", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("cancelled", ctypes.c_uint64), ("agent_steps", ctypes.c_uint64), ("iterations", ctypes.c_uint64),
                 ("launches", ctypes.c_uint64), ("hbm_in_use", ctypes.c_size_t), ("hbm_peak", ctypes.c_size_t),
                 ("active", ctypes.c_uint32), ("pending", ctypes.c_uint32), ("busy_s", ctypes.c_double)]
 
@@ -144,6 +144,8 @@ def lib():
             "amb_server_counts": (st, [vp, u64, vp, sz, ctypes.POINTER(sz)]),
             "amb_server_read_column": (st, [vp, u64, ctypes.c_int, vp, sz]),
             "amb_server_release": (st, [vp, u64]),
+            "amb_server_cancel": (st, [vp, u64]),
+            "amb_debug_fail_creates": (st, [u32]),
             "amb_server_drain": (st, [vp, ctypes.c_double]),
             "amb_server_stats": (st, [vp, ctypes.POINTER(amb_server_report)]),
             "amb_server_destroy": (st, [vp]),
@@ -619,6 +621,9 @@ class Server:
         amb_server_release(self.handle, ticket)
         self.specs.pop(ticket, None)
 
+    def cancel(self, ticket):
+        _check(lib().amb_server_cancel(self.handle, int(ticket)))
+
     def drain(self, timeout_s=600.0):
         amb_server_drain(self.handle, timeout_s)
 
@@ -842,3 +847,8 @@ class Log:
             self.close()
         except Exception:
             pass
+
+
+def amb_debug_fail_creates(k):
+    """Test hook: the next k population creations fail with AMB_ENOMEM."""
+    _check(lib().amb_debug_fail_creates(int(k)))

@@ -129,6 +129,7 @@ void sir_batch_finish(SirBatch &sb, amb_pop **pops, const uint32_t *steps, uint3
 void sir_batch_release(SirBatch &sb, cudaStream_t s);
 
 amb_status check_params(amb_model model, const amb_params *p, uint64_t seed);
+bool injected_create_failure();
 
 // Advance pops[i] by ks[i] steps with the batched launches (optionally as one
 // CUDA graph); *launches += kernels launched, *ms = device time.

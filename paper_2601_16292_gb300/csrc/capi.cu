@@ -1,6 +1,7 @@
 // capi.cu -- extern "C" entry points of include/amb.h: argument checks,
 // population lifetime, dispatch to the model kernels, read-back, invariants
 // and statistics.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -273,6 +274,17 @@ amb_status amb_sir_thresholds(double beta, double gamma, uint32_t cap, uint32_t 
 }  // extern "C"
 
 namespace amb {
+static std::atomic<uint32_t> g_fail_creates{0};
+
+// consume one injected creation failure, if any are armed
+bool injected_create_failure()
+{
+    uint32_t k = g_fail_creates.load();
+    while (k > 0)
+        if (g_fail_creates.compare_exchange_weak(k, k - 1)) return true;
+    return false;
+}
+
 cudaMemPool_t library_pool()
 {
     static std::mutex mu;
@@ -351,6 +363,7 @@ amb_status amb_create(amb_model model, const amb_params *p, uint64_t seed, uint3
     if (!p || !out) return fail(AMB_EINVAL, "null pointer");
     *out = nullptr;
     AMB_TRY(check_params(model, p, seed));
+    if (injected_create_failure()) return fail(AMB_ENOMEM, "injected creation failure");
     const uint32_t L = p->grid_side;
     amb_pop *pop = new (std::nothrow) amb_pop();
     if (!pop) return fail(AMB_ENOMEM, "host allocation failed");
@@ -914,6 +927,12 @@ __global__ void wait_selfcheck_kernel(uint64_t *status, uint32_t *err, unsigned 
 }  // namespace
 
 extern "C" {
+
+amb_status amb_debug_fail_creates(uint32_t k)
+{
+    g_fail_creates.store(k);
+    return AMB_OK;
+}
 
 amb_status amb_selfcheck_wait_timeout(void *cuda_stream, double *waited_s)
 {

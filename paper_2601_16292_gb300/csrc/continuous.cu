@@ -552,6 +552,7 @@ extern "C" amb_status amb_create_continuous(amb_model model, const amb_cparams *
     if (!p || !out) return fail(AMB_EINVAL, "null pointer");
     *out = nullptr;
     AMB_TRY(check_cparams(model, p, seed));
+    if (injected_create_failure()) return fail(AMB_ENOMEM, "injected creation failure");
     amb_pop *pop = new (std::nothrow) amb_pop();
     if (!pop) return fail(AMB_ENOMEM, "host allocation failed");
     pop->model = model;

@@ -15,6 +15,7 @@
 // Memory accounting uses amb_job_bytes (host arithmetic), plus a fixed reserve
 // for the per-iteration launch tables and wide band counters.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -51,6 +52,7 @@ struct ServerJob {
     uint32_t done_steps = 0;
     amb_status status = AMB_OK;
     bool finished = false;
+    std::atomic<bool> cancel{false};  // set by amb_server_cancel while the job runs
     std::vector<int64_t> series;
     std::vector<int32_t> col_a, col_b;  // wealth, or x and y
     std::vector<uint8_t> col_state;
@@ -69,6 +71,7 @@ struct amb_server {
     std::unordered_map<uint64_t, ServerJob *> jobs;  // every job not released
     std::vector<ServerJob *> active;                 // worker thread only
     uint64_t next_ticket = 1;
+    uint64_t cancelled_running = 0;  // jobs cancelled after admission
     size_t in_use = 0, peak = 0;
     amb_server_report rep{};
     bool stop = false;
@@ -144,6 +147,9 @@ void finish_job(amb_server *S, ServerJob *j, amb_status st)
     if (st == AMB_OK) {
         S->rep.completed += 1;
         S->rep.agent_steps += (uint64_t)j->job.params.n * j->done_steps;
+    } else if (st == AMB_ECANCELED) {
+        S->rep.cancelled += 1;
+        S->cancelled_running += 1;
     } else {
         S->rep.failed += 1;
     }
@@ -216,7 +222,9 @@ void worker_loop(amb_server *S)
                 continue;
             }
             j->done_steps += ks[q];
-            if (words[q]) {
+            if (j->cancel.load()) {
+                finish_job(S, j, AMB_ECANCELED);
+            } else if (words[q]) {
                 finish_job(S, j, (words[q] & ERR_TIMEOUT) ? AMB_ETIMEOUT : AMB_EINVARIANT);
             } else if (j->done_steps == j->job.steps) {
                 finish_job(S, j, AMB_OK);
@@ -384,6 +392,27 @@ amb_status amb_server_read_column(amb_server *S, uint64_t ticket, amb_col col, v
     return AMB_OK;
 }
 
+amb_status amb_server_cancel(amb_server *S, uint64_t ticket)
+{
+    if (!S) return fail(AMB_EINVAL, "null server");
+    std::lock_guard<std::mutex> lk(S->mu);
+    ServerJob *j = find_locked(S, ticket);
+    if (!j) return fail(AMB_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    if (j->finished) return AMB_OK;
+    auto it = std::find(S->pending.begin(), S->pending.end(), j);
+    if (it != S->pending.end()) {  // still queued: ends now
+        S->pending.erase(it);
+        j->status = AMB_ECANCELED;
+        j->t_done = S->now();
+        j->finished = true;
+        S->rep.cancelled += 1;
+        S->cv_done.notify_all();
+        return AMB_OK;
+    }
+    j->cancel.store(true);  // admitted: ends after the current iteration
+    return AMB_OK;
+}
+
 amb_status amb_server_release(amb_server *S, uint64_t ticket)
 {
     if (!S) return fail(AMB_EINVAL, "null server");
@@ -402,10 +431,11 @@ amb_status amb_server_drain(amb_server *S, double timeout_s)
     std::unique_lock<std::mutex> lk(S->mu);
     const auto until = std::chrono::steady_clock::now() + std::chrono::duration<double>(std::max(timeout_s, 0.0));
     const bool ok = S->cv_done.wait_until(lk, until, [&] {
-        return S->rep.completed + S->rep.failed == S->rep.submitted;
+        return S->rep.completed + S->rep.failed + S->rep.cancelled == S->rep.submitted;
     });
-    return ok ? AMB_OK : fail(AMB_ETIMEOUT, "%llu jobs still queued or running",
-                              (unsigned long long)(S->rep.submitted - S->rep.completed - S->rep.failed));
+    return ok ? AMB_OK
+              : fail(AMB_ETIMEOUT, "%llu jobs still queued or running",
+                     (unsigned long long)(S->rep.submitted - S->rep.completed - S->rep.failed - S->rep.cancelled));
 }
 
 amb_status amb_server_stats(amb_server *S, amb_server_report *out)
@@ -416,7 +446,7 @@ amb_status amb_server_stats(amb_server *S, amb_server_report *out)
     out->hbm_in_use = S->in_use;
     out->hbm_peak = S->peak;
     out->pending = (uint32_t)S->pending.size();
-    out->active = (uint32_t)(S->rep.admitted - S->rep.completed - S->rep.failed);
+    out->active = (uint32_t)(S->rep.admitted - S->rep.completed - S->rep.failed - S->cancelled_running);
     return AMB_OK;
 }
 

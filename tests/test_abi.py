@@ -125,3 +125,21 @@ def test_job_bytes_rejects_what_create_rejects():
         amb.amb_job_bytes(amb.make_job("sir", 10, seed=1, steps=1, L=4, beta=0.5, gamma=0.1, n0=11))
     with pytest.raises(amb.AmbError):
         amb.amb_job_bytes(amb.make_job("walk", 10, seed=1 << 33, steps=1, L=4))
+
+
+def test_injected_creation_failures_on_the_host():
+    """The fault-injection hook fails creations before any device call."""
+    amb.amb_debug_fail_creates(2)
+    try:
+        for _ in range(2):
+            with pytest.raises(amb.AmbError) as e:
+                amb.amb_create("wealth", amb.amb_params(n=10, grid_side=1, w_init=1), 0)
+            assert e.value.status == amb.AMB_ENOMEM
+            assert "injected" in str(e.value)
+        # the hook is spent: the next call is checked as usual (continuous
+        # models are refused by amb_create before any device call)
+        with pytest.raises(amb.AmbError) as e:
+            amb.amb_create("csir", amb.amb_params(n=10), 0)
+        assert e.value.status == amb.AMB_EINVAL
+    finally:
+        amb.amb_debug_fail_creates(0)

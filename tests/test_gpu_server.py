@@ -137,3 +137,64 @@ def test_destroy_with_work_in_flight(stream):
     time.sleep(0.01)
     srv.close()  # stops after the current iteration and frees everything
     torch.cuda.synchronize()
+
+
+def test_injected_creation_failures_fail_only_those_jobs(stream):
+    jobs = [dict(model="wealth", n=2000 + i, seed=i, steps=7) for i in range(5)]
+    srv = amb.Server(RESERVE + (64 << 20), stream, max_active=1)
+    amb.amb_debug_fail_creates(2)
+    try:
+        tickets = [srv.submit(j) for j in jobs]
+        res = [srv.wait(t, 60.0) for t in tickets]
+    finally:
+        amb.amb_debug_fail_creates(0)
+    assert [r["status"] for r in res] == [amb.AMB_ENOMEM] * 2 + [amb.AMB_OK] * 3
+    for t, j, r in list(zip(tickets, jobs, res))[2:]:
+        assert np.array_equal(srv.counts(t), _lone(j, stream)["counts"])
+    st = srv.stats()
+    assert st["failed"] == 2 and st["completed"] == 3 and st["hbm_in_use"] == 0
+    srv.close()
+
+
+def test_cancel_queued_and_running_jobs(stream):
+    srv = amb.Server(RESERVE + (400 << 20), stream, max_active=1, chunk_steps=1)
+    long_job = dict(model="sir", n=1_000_000, L=1291, beta=0.05, gamma=0.02, n0=1000, seed=1, steps=2000)
+    a = srv.submit(long_job)
+    b = srv.submit(dict(model="walk", n=1000, L=41, seed=2, steps=5))   # queued behind a (one slot)
+    c = srv.submit(dict(model="wealth", n=1000, seed=3, steps=5))
+    srv.cancel(b)
+    rb = srv.wait(b, 5.0)
+    assert rb["status"] == amb.AMB_ECANCELED and rb["admit_s"] < 0
+    for _ in range(200):  # a is running once it has been admitted
+        if srv.stats()["admitted"] >= 1:
+            break
+        time.sleep(0.01)
+    srv.cancel(a)
+    ra = srv.wait(a, 60.0)
+    assert ra["status"] == amb.AMB_ECANCELED and ra["steps"] < 2000
+    rc = srv.wait(c, 60.0)
+    assert rc["status"] == amb.AMB_OK and rc["steps"] == 5
+    srv.cancel(c)  # finished jobs are left as they are
+    assert srv.wait(c, 1.0)["status"] == amb.AMB_OK
+    st = srv.stats()
+    assert st["cancelled"] == 2 and st["completed"] == 1 and st["active"] == 0 and st["hbm_in_use"] == 0
+    with pytest.raises(amb.AmbError):
+        srv.counts(a)
+    srv.close()
+
+
+def test_serving_trace_sample_equals_oracle(stream):
+    """Jobs of the serving trace (sizes capped at 20,000 agents so that the
+    oracle stays quick) served together, each equal to the oracle."""
+    jobs = workloads.scaled(workloads.serve_trace(n_jobs=30)[1], 20_000)
+    srv = amb.Server(RESERVE + (1 << 30), stream, chunk_steps=16)
+    tickets = [srv.submit(j, keep_columns=True) for j in jobs]
+    srv.drain(300.0)
+    for t, j in zip(tickets, jobs):
+        kw = {k: v for k, v in j.items() if k not in ("model", "steps")}
+        o = oracle.Population(j["model"], **kw).step(j["steps"])
+        assert np.array_equal(srv.counts(t), o.counts()), j
+        cols = ("wealth",) if j["model"] == "wealth" else (("x", "y", "state") if j["model"] == "sir" else ("x", "y"))
+        for c in cols:
+            assert np.array_equal(srv.column(t, c), getattr(o, "w" if c == "wealth" else c)), (j, c)
+    srv.close()
