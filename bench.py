@@ -75,9 +75,12 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle samples while the timed region runs."""
+    """nvidia-smi clock / throttle readings (every 10 ms, timestamped) while
+    the GPU runs the step kernel; stop() keeps those inside the timed window
+    (falling back to the whole loaded period when the window is shorter than
+    the sampling interval)."""
 
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -85,20 +88,28 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
+        self.window = None
 
-    def start(self):
+    def start(self, wait_first=2.0):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "10"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < wait_first:
+                time.sleep(0.005)
         except Exception:
             self.proc = None
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, t0, t1):
+        """The timed region, in host time."""
+        self.window = (t0, t1)
 
     def stop(self):
         if self.proc is None:
@@ -108,24 +119,24 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        rows = []
+        for t, ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
+                rows.append((t, float(f[2]), float(f[3]), [nm for nm, v in zip(names, f[6:10]) if v.lower() == "active"]))
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
+        inside = [r for r in rows if self.window and self.window[0] - 0.01 <= r[0] <= self.window[1] + 0.01]
+        use = inside if inside else rows
+        if not use:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        sm.sort()
-        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+        sm = sorted(r[1] for r in use)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[2] for r in use),
+                "reasons": sorted({x for r in use for x in r[3]}), "samples": len(use),
+                "samples_in_timed_window": len(inside)}
 
 
 def dist_setup(n_gpus, backend="nccl"):
@@ -174,22 +185,28 @@ def sum_over_ranks(world, v, device):
 
 
 # --------------------------------------------------------------- GPU arm ----
-def time_sir(amb, torch, steps, warmup, rank, stream):
+def time_sir(amb, torch, steps, warmup, rank, stream, world=1, sampler=None):
     c = SIR_CFG
     pop = amb.Population("sir", c["n"], seed=c["seed"], rep=rank, L=c["L"], beta=c["beta"], gamma=c["gamma"],
                          n0=c["n0"], stream=stream)
+    if sampler is not None:
+        sampler.start()
     for _ in range(warmup):
         pop.step(1)
     pop.synchronize()
     launches0 = amb.amb_launch_count(pop.handle)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    barrier(world)
     torch.cuda.synchronize()
+    t_start = time.time()
     with torch.cuda.stream(stream):
         ev[0].record(stream)
         for k in range(steps):
             amb.amb_step(pop.handle, 1)
             ev[k + 1].record(stream)
     torch.cuda.synchronize()
+    if sampler is not None:
+        sampler.mark(t_start, time.time())
     per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
     total_ms = ev[0].elapsed_time(ev[steps])
     launches = amb.amb_launch_count(pop.handle) - launches0
@@ -540,13 +557,10 @@ def gpu_arm(args):
     paper_models = None if only_sir else paper_models_bench(amb, torch, stream)
 
     sampler = ClockSampler(local)
-    barrier(world)
+    total_ms, per, launches, inv, path = time_sir(amb, torch, args.steps, args.warmup, rank, stream, world, sampler)
     torch.cuda.synchronize()
-    sampler.start()
-    total_ms, per, launches, inv, path = time_sir(amb, torch, args.steps, args.warmup, rank, stream)
-    torch.cuda.synchronize()
-    barrier(world)
     clocks = sampler.stop()
+    barrier(world)
     total_ms_max = max_over_ranks(world, total_ms, device)
     agent_steps = sum_over_ranks(world, float(SIR_CFG["n"]) * args.steps, device)
     e2e = None if only_sir else run_e2e(amb, torch, max(args.steps, 3), rank, stream)
@@ -652,7 +666,7 @@ def reference_arm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="amb", choices=["amb", "reference"])
     ap.add_argument("--only", default="all", choices=["all", "sir", "sweep", "serve", "views", "paper"],
