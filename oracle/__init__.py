@@ -69,9 +69,11 @@ def lib():
         L.orc_cwalk_step.argtypes = [u32, f32, f32, f32, u32, u32, u32, f32p, f32p]
         L.orc_csir_step.argtypes = [u32, f32, f32, f32, f32, u32, u32, u32, u32p, u32, u32, f32p, f32p, u8p, i32p, i64p]
         L.orc_log_flush.argtypes = [ctypes.c_int, vp, u32, i32p, i64p, u32]
+        L.orc_view_where.argtypes = [ctypes.c_int, vp, u32, i32p, u32, ctypes.c_int, i64, i32p, u32p]
+        L.orc_view_add_values.argtypes = [ctypes.c_int, vp, u32, i32p, i32p, u32]
         L.orc_grid_walk_step.argtypes = [u32, u32p, ctypes.c_int, ctypes.c_int, u32, ctypes.POINTER(i32p), u32, u32,
                                          u32]
-        for f in ("orc_log_flush", "orc_grid_walk_step", "orc_cwalk_step", "orc_csir_step", "orc_col_map", "orc_col_map_col", "orc_where", "orc_view_map", "orc_view_draw",
+        for f in ("orc_view_where", "orc_view_add_values", "orc_log_flush", "orc_grid_walk_step", "orc_cwalk_step", "orc_csir_step", "orc_col_map", "orc_col_map_col", "orc_where", "orc_view_map", "orc_view_draw",
                   "orc_wealth_step", "orc_walk_step", "orc_sir_thresholds", "orc_sir_step",
                   "orc_cell_index", "orc_occupancy", "orc_gini", "orc_curve_moments"):
             getattr(L, f).restype = ctypes.c_int
@@ -344,3 +346,22 @@ def grid_walk_step(coords, sizes, moore, torus, seed, rep, t):
         if c is not a:
             c[:] = a
     return coords
+
+
+def view_where(col, ids, cmp, s):
+    """The listed ids (list order, repeats kept) with col[id] CMP s."""
+    ids = np.ascontiguousarray(ids, dtype=np.int32)
+    out = np.zeros(max(ids.size, 1), dtype=np.int32)
+    k = np.zeros(1, dtype=np.uint32)
+    _check(lib().orc_view_where(_dtype_code(col), col.ctypes.data, col.size, _p(ids, ctypes.c_int32), ids.size,
+                                CMPS[cmp], int(s), _p(out, ctypes.c_int32), _p(k, ctypes.c_uint32)), "view_where")
+    return out[:int(k[0])]
+
+
+def view_add_values(col, ids, values):
+    """col[ids[j]] += values[j] for every j (repeats accumulate)."""
+    ids = np.ascontiguousarray(ids, dtype=np.int32)
+    values = np.ascontiguousarray(values, dtype=np.int32)
+    _check(lib().orc_view_add_values(_dtype_code(col), col.ctypes.data, col.size, _p(ids, ctypes.c_int32),
+                                     _p(values, ctypes.c_int32), ids.size), "view_add_values")
+    return col

@@ -686,3 +686,33 @@ int orc_grid_walk_step(uint32_t d, const uint32_t *sizes, int moore, int torus, 
     }
     return ORC_OK;
 }
+
+/* Filtered view of a view: the listed ids (in list order, repeats kept) whose
+ * value satisfies col CMP s -- where(A).where(B) is the conjunction A and B. */
+int orc_view_where(int dtype, const void *col, uint32_t n, const int32_t *ids, uint32_t k, int cmp, int64_t s,
+                   int32_t *out, uint32_t *count)
+{
+    if ((dtype != DT_I32 && dtype != DT_U8) || cmp < 0 || cmp > 5 || (k && (!col || !ids || !out)) || !count)
+        return ORC_EINVAL;
+    uint32_t m = 0;
+    for (uint32_t j = 0; j < k; ++j) {
+        if (ids[j] < 0 || (uint32_t)ids[j] >= n) return ORC_EINVAL;
+        if (compare(col_get(dtype, col, (uint32_t)ids[j]), cmp, s)) out[m++] = ids[j];
+    }
+    *count = m;
+    return ORC_OK;
+}
+
+/* scatter_add with one value per listed id: col[ids[j]] += values[j] (in the
+ * column's wrapping arithmetic; repeated ids accumulate). */
+int orc_view_add_values(int dtype, void *col, uint32_t n, const int32_t *ids, const int32_t *values, uint32_t k)
+{
+    if ((dtype != DT_I32 && dtype != DT_U8) || (k && (!col || !ids || !values))) return ORC_EINVAL;
+    for (uint32_t j = 0; j < k; ++j)
+        if (ids[j] < 0 || (uint32_t)ids[j] >= n) return ORC_EINVAL;
+    for (uint32_t j = 0; j < k; ++j) {
+        uint32_t i = (uint32_t)ids[j];
+        col_set(dtype, col, i, apply_op(dtype, col_get(dtype, col, i), 1, values[j]));
+    }
+    return ORC_OK;
+}

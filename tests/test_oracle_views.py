@@ -117,3 +117,28 @@ def test_wealth_by_views_equals_wealth_rule(n, seed, rep, w_init):
         _wealth_step_by_views(w, seed, rep, t)
         ref.step(1)
         assert np.array_equal(w, ref.w), t
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.uint8])
+def test_view_where_is_boolean_indexing(dtype):
+    col = RNG.integers(0, 9, 500).astype(dtype)
+    ids = RNG.integers(0, 500, 2000).astype(np.int32)  # a scatter view with repeats
+    for cmp, s in [(">", 4), ("==", 3), ("!=", 0), ("<=", 2)]:
+        v = col[ids].astype(np.int64)
+        pred = {">": v > s, "==": v == s, "!=": v != s, "<=": v <= s}[cmp]
+        assert np.array_equal(oracle.view_where(col, ids, cmp, s), ids[pred])
+    # where(A).where(B) == where(A and B)
+    other = RNG.integers(0, 5, 500).astype(np.int32)
+    a = oracle.where(col, ">", 2)
+    ab = oracle.view_where(other, a, "==", 1)
+    assert np.array_equal(ab, np.flatnonzero((col.astype(np.int64) > 2) & (other == 1)))
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.uint8])
+def test_view_add_values_is_add_at(dtype):
+    col = RNG.integers(0, 100, 64).astype(dtype)
+    ids = RNG.integers(0, 64, 700).astype(np.int32)
+    vals = RNG.integers(-1000, 1000, 700).astype(np.int32)
+    want = col.copy()
+    np.add.at(want, ids, vals.astype(dtype))
+    assert np.array_equal(oracle.view_add_values(col.copy(), ids, vals), want)
