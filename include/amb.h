@@ -487,6 +487,14 @@ amb_status amb_view_from_ids(amb_table *t, const int32_t *ids, size_t k, int ids
  * id, range >= 2); otherwise m = range and r = r' (range >= 1). */
 amb_status amb_view_draw(amb_view *v, uint64_t seed, uint32_t replicate, uint32_t step, uint32_t word, uint32_t range,
                          int exclude_self, amb_view **out);
+/* A view of a view: the ids v lists (in v's order, repeats kept) whose value
+ * satisfies col CMP scalar, so where(A) followed by amb_view_where(B) is the
+ * conjunction of A and B.  Asynchronous; the length stays on the device. */
+amb_status amb_view_where(amb_view *v, int col, amb_cmp cmp, int64_t scalar, amb_view **out);
+/* scatter_add with one value per listed id: col[id_j] += values[j] for the
+ * view's entries j (device int32 array of n_values >= the view's length;
+ * shorter arrays are reported by amb_table_synchronize). */
+amb_status amb_view_scatter_add_values(amb_view *v, int col, const int32_t *values, size_t n_values);
 /* Update the rows a view lists: col[id] = col[id] OP scalar per listed id. */
 amb_status amb_view_map(amb_view *v, int col, amb_op op, int64_t scalar);
 /* amb_view_map with AMB_OP_ADD: duplicate ids accumulate. */

@@ -163,6 +163,8 @@ def lib():
             "amb_view_draw": (st, [vp, u64, u32, u32, u32, u32, ctypes.c_int, ctypes.POINTER(vp)]),
             "amb_view_map": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64]),
             "amb_view_scatter_add": (st, [vp, ctypes.c_int, ctypes.c_int64]),
+            "amb_view_where": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(vp)]),
+            "amb_view_scatter_add_values": (st, [vp, ctypes.c_int, vp, sz]),
             "amb_view_count": (st, [vp, ctypes.POINTER(sz)]),
             "amb_view_ids": (st, [vp, vp, sz, ctypes.c_int, ctypes.POINTER(sz)]),
             "amb_view_destroy": (st, [vp]),
@@ -742,8 +744,22 @@ class View:
         return self
 
     def scatter_add(self, name, value):
-        _check(lib().amb_view_scatter_add(self.handle, self.table.col(name), int(value)))
+        """scatter_add with one value for every listed id, or with a device
+        int32 tensor of per-entry values."""
+        if hasattr(value, "data_ptr"):
+            p, dev, k, _ = _buffer(value)
+            if not dev:
+                raise ValueError("per-entry values must be a device tensor")
+            _check(lib().amb_view_scatter_add_values(self.handle, self.table.col(name), p, k))
+        else:
+            _check(lib().amb_view_scatter_add(self.handle, self.table.col(name), int(value)))
         return self
+
+    def where(self, name, cmp, scalar):
+        """The listed ids whose value satisfies name CMP scalar (a view)."""
+        h = ctypes.c_void_p()
+        _check(lib().amb_view_where(self.handle, self.table.col(name), CMPS[cmp], int(scalar), ctypes.byref(h)))
+        return View(self.table, h)
 
     def draw(self, seed, rep, step, word=0, rng=None, exclude_self=True):
         h = ctypes.c_void_p()

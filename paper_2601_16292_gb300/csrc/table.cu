@@ -215,6 +215,94 @@ __global__ void __launch_bounds__(kWhereNT) where_kernel(const T *__restrict__ c
     }
 }
 
+// A view of a view: the listed ids (list order) whose value satisfies the
+// predicate.  Same tiling as where_kernel; the column is read through the ids.
+constexpr int kVwNT = 256;
+constexpr int kVwItems = 16;
+constexpr uint32_t kVwTile = kVwNT * kVwItems;
+
+template <int CMP, class T>
+__global__ void __launch_bounds__(kVwNT) view_where_kernel(const T *__restrict__ c, const int32_t *__restrict__ in,
+                                                            const uint32_t *__restrict__ in_count, int64_t s,
+                                                            int32_t *__restrict__ ids, uint32_t *__restrict__ count,
+                                                            uint32_t n_tiles, unsigned long long *tickets,
+                                                            uint32_t parity, uint64_t *status, uint32_t epoch,
+                                                            uint32_t *err)
+{
+    __shared__ uint32_t s_tile, s_prefix;
+    __shared__ uint32_t s_warp[kVwNT / 32 + 1];
+    __shared__ int32_t s_ids[kVwTile];
+    const uint32_t tid = threadIdx.x, k = *in_count;
+    if (blockIdx.x == 0 && tid == 0) tickets[parity ^ 1u] = 0ull;
+    for (;;) {
+        if (tid == 0) s_tile = (uint32_t)atomicAdd(&tickets[parity], 1ull);
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        __syncthreads();
+        if (tile >= n_tiles) break;
+        const uint32_t i0 = tile * kVwTile + tid * kVwItems;
+        uint32_t bits = 0;
+        int32_t id[kVwItems];
+#pragma unroll
+        for (int q = 0; q < kVwItems; ++q) {
+            id[q] = (i0 + q < k) ? in[i0 + q] : -1;
+            if (id[q] >= 0 && compare<CMP>((int64_t)c[id[q]], s)) bits |= 1u << q;
+        }
+        uint32_t total;
+        const uint32_t ex = block_exclusive_scan<kVwNT>(__popc(bits), s_warp, &total);
+        uint32_t pos = ex;
+#pragma unroll
+        for (int q = 0; q < kVwItems; ++q)
+            if (bits & (1u << q)) s_ids[pos++] = id[q];
+        if (tid < 32) {
+            const uint32_t pre = warp_lookback(status, tile, epoch, total, err);
+            if (tid == 0) s_prefix = pre;
+        }
+        __syncthreads();
+        const uint32_t pre = s_prefix;
+        for (uint32_t j = tid; j < total; j += kVwNT) ids[pre + j] = s_ids[j];
+        if (tile == n_tiles - 1u && tid == 0) *count = pre + total;
+        __syncthreads();
+    }
+}
+
+// scatter_add with one value per listed id
+__global__ void __launch_bounds__(256) view_add_values_i32_kernel(int32_t *__restrict__ c, const int32_t *__restrict__ ids,
+                                                                  const uint32_t *__restrict__ count,
+                                                                  const int32_t *__restrict__ vals, uint32_t n_vals,
+                                                                  uint32_t *err)
+{
+    const uint32_t k = *count;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && k > n_vals) atomicOr(err, ERR_RANGE);
+    const uint32_t m = k < n_vals ? k : n_vals;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+        atomicAdd(reinterpret_cast<unsigned int *>(c + ids[i]), (unsigned int)vals[i]);
+}
+
+__global__ void __launch_bounds__(256) view_add_values_u8_kernel(uint8_t *__restrict__ c, const int32_t *__restrict__ ids,
+                                                                 const uint32_t *__restrict__ count,
+                                                                 const int32_t *__restrict__ vals, uint32_t n_vals,
+                                                                 uint32_t *err)
+{
+    const uint32_t k = *count;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && k > n_vals) atomicOr(err, ERR_RANGE);
+    const uint32_t m = k < n_vals ? k : n_vals;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        const uint32_t id = (uint32_t)ids[i], sh = 8u * (id & 3u);
+        const uint8_t add = (uint8_t)vals[i];
+        uint32_t *word = reinterpret_cast<uint32_t *>(c + (id & ~3u));
+        uint32_t old = *reinterpret_cast<volatile uint32_t *>(word);
+        bool done = false;
+        for (uint32_t attempt = 0; attempt < (1u << 24) && !done; ++attempt) {
+            const uint32_t nv = (old & ~(0xFFu << sh)) | ((uint32_t)(uint8_t)((uint8_t)(old >> sh) + add) << sh);
+            const uint32_t prev = atomicCAS(word, old, nv);
+            done = (prev == old);
+            old = prev;
+        }
+        if (!done) atomicOr(err, ERR_TIMEOUT);
+    }
+}
+
 // ---------------------------------------------------------- view update ---
 // Bounded compare-and-swap update of one word (lock-free: a failed attempt
 // means another thread's update went in; the bound only guards against a
@@ -833,6 +921,83 @@ amb_status amb_view_draw(amb_view *v, uint64_t seed, uint32_t replicate, uint32_
         return fail(AMB_ECUDA, "draw launch failed");
     }
     *out = r;
+    return AMB_OK;
+}
+
+amb_status amb_view_where(amb_view *v, int col, amb_cmp cmp, int64_t scalar, amb_view **out)
+{
+    if (!v || !out) return fail(AMB_EINVAL, "null pointer");
+    *out = nullptr;
+    amb_table *t = v->t;
+    Column *c = nullptr;
+    AMB_TRY(get_col(t, col, &c));
+    if ((int)cmp < 0 || (int)cmp > AMB_CMP_GE) return fail(AMB_EINVAL, "unknown comparison %d", (int)cmp);
+    amb_view *r = nullptr;
+    AMB_TRY(new_view(t, v->capacity, v->unique, &r));
+    cudaStream_t st = t->stream;
+    amb_status res = AMB_OK;
+    if (v->capacity == 0) {
+        if (cudaMemsetAsync(r->count, 0, sizeof(uint32_t), st) != cudaSuccess) res = fail(AMB_ECUDA, "memset failed");
+    } else {
+        const uint32_t n_tiles = (v->capacity + kVwTile - 1u) / kVwTile;
+        res = t->lb.ensure(n_tiles, st);
+        if (res == AMB_OK) {
+            uint32_t parity, epoch;
+            t->lb.next(&parity, &epoch);
+            const unsigned g = std::min<uint32_t>(n_tiles, 152u * 8u);
+#define VW_CASE(C, T)                                                                                               \
+    case C:                                                                                                         \
+        view_where_kernel<C, T><<<g, kVwNT, 0, st>>>(static_cast<const T *>(c->ptr), v->ids, v->count, scalar, r->ids, \
+                                                     r->count, n_tiles, t->lb.tickets, parity, t->lb.status, epoch,  \
+                                                     t->err);                                                        \
+        break;
+            if (c->dtype == AMB_DT_I32) {
+                switch (cmp) {
+                    VW_CASE(AMB_CMP_EQ, int32_t)
+                    VW_CASE(AMB_CMP_NE, int32_t)
+                    VW_CASE(AMB_CMP_LT, int32_t)
+                    VW_CASE(AMB_CMP_LE, int32_t)
+                    VW_CASE(AMB_CMP_GT, int32_t)
+                    VW_CASE(AMB_CMP_GE, int32_t)
+                }
+            } else {
+                switch (cmp) {
+                    VW_CASE(AMB_CMP_EQ, uint8_t)
+                    VW_CASE(AMB_CMP_NE, uint8_t)
+                    VW_CASE(AMB_CMP_LT, uint8_t)
+                    VW_CASE(AMB_CMP_LE, uint8_t)
+                    VW_CASE(AMB_CMP_GT, uint8_t)
+                    VW_CASE(AMB_CMP_GE, uint8_t)
+                }
+            }
+#undef VW_CASE
+            if (cudaGetLastError() != cudaSuccess) res = fail(AMB_ECUDA, "view_where launch failed");
+        }
+    }
+    if (res != AMB_OK) {
+        amb_view_destroy(r);
+        return res;
+    }
+    *out = r;
+    return AMB_OK;
+}
+
+amb_status amb_view_scatter_add_values(amb_view *v, int col, const int32_t *values, size_t n_values)
+{
+    if (!v || (!values && n_values)) return fail(AMB_EINVAL, "null pointer");
+    amb_table *t = v->t;
+    Column *c = nullptr;
+    AMB_TRY(get_col(t, col, &c));
+    if (n_values > 0xFFFFFFFFu) return fail(AMB_EINVAL, "too many values");
+    if (v->capacity == 0) return AMB_OK;
+    const unsigned g = map_grid(v->capacity);
+    if (c->dtype == AMB_DT_I32)
+        view_add_values_i32_kernel<<<g, 256, 0, t->stream>>>(static_cast<int32_t *>(c->ptr), v->ids, v->count, values,
+                                                             (uint32_t)n_values, t->err);
+    else
+        view_add_values_u8_kernel<<<g, 256, 0, t->stream>>>(static_cast<uint8_t *>(c->ptr), v->ids, v->count, values,
+                                                            (uint32_t)n_values, t->err);
+    AMB_TRY_CUDA(cudaGetLastError());
     return AMB_OK;
 }
 

@@ -176,3 +176,45 @@ def test_errors(stream):
     empty.map("c", "add", 1)
     assert empty.read("c").numel() == 0
     empty.close()
+
+
+@pytest.mark.parametrize("n", [0, 7, 4096, 4100, 3 * 4096 + 5, 300_001])
+def test_view_of_view_and_conjunctions(stream, n):
+    a = RNG.integers(0, 9, n).astype(np.int32)
+    b = RNG.integers(0, 4, n).astype(np.uint8)
+    t = _table(n, stream, {"a": a, "b": b})
+    with t.where("a", ">", 3) as va, va.where("b", "==", 1) as vab:
+        assert np.array_equal(vab.ids(), np.flatnonzero((a > 3) & (b == 1)))
+    # over a scatter view: list order and repeats kept
+    ids = RNG.integers(0, max(n, 1), 3 * n).astype(np.int32) if n else np.zeros(0, dtype=np.int32)
+    with t.at(ids) as vs, vs.where("a", "<=", 2) as vsf:
+        assert np.array_equal(vsf.ids(), oracle.view_where(a, ids, "<=", 2))
+    t.close()
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.uint8])
+def test_scatter_add_values(stream, dtype):
+    n = 5000
+    col = _rand(dtype, n)
+    t = _table(n, stream, {"c": col})
+    ids = RNG.integers(0, 200, 30_000).astype(np.int32)
+    vals = RNG.integers(-2 ** 31, 2 ** 31, 30_000).astype(np.int32)
+    with t.at(ids) as v:
+        v.scatter_add("c", torch.from_numpy(vals).cuda())
+    want = oracle.view_add_values(col.copy(), ids, vals)
+    assert np.array_equal(t.read("c").numpy(), want)
+    # per-entry values through a filtered view whose length lives on the device
+    with t.where("c", ">", 10) as f:
+        k = f.count()
+        fv = RNG.integers(0, 5, k).astype(np.int32)
+        fids = f.ids()
+        f.scatter_add("c", torch.from_numpy(fv).cuda())
+    oracle.view_add_values(want, fids, fv)
+    assert np.array_equal(t.read("c").numpy(), want)
+    # too few values: reported, the table stays usable
+    with t.at(np.arange(10, dtype=np.int32)) as v:
+        v.scatter_add("c", torch.zeros(5, dtype=torch.int32).cuda())
+        with pytest.raises(amb.AmbError):
+            t.synchronize()
+    t.synchronize()
+    t.close()
