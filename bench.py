@@ -48,9 +48,10 @@ def sir_layout_bytes_per_agent_step(n, L):
     return 16.0 + 4.0 * L * L / n
 
 
-def profiled_traffic(key):
-    """DRAM bytes (read + write) per launch of the kernel from the committed ncu
-    capture, or None when the kernel's sources changed since the capture."""
+def profiled(key, field="dram_bytes_per_launch"):
+    """A per-launch figure of the kernel from the committed ncu capture (DRAM
+    bytes read + written by default), or None when the kernel's sources
+    changed since the capture."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
@@ -59,9 +60,13 @@ def profiled_traffic(key):
         for p in d["source_files"]:
             with open(os.path.join(ROOT, p), "rb") as f:
                 h.update(f.read())
-        return d["dram_bytes_per_launch"] if h.hexdigest() == d["source_sha1"] else None
+        return d.get(field) if h.hexdigest() == d["source_sha1"] else None
     except Exception:
         return None
+
+
+def profiled_traffic(key):
+    return profiled(key)
 
 
 def load_peaks():
@@ -581,6 +586,16 @@ def gpu_arm(args):
     achieved = b_alg * n / (step_ms / 1e3) / 1e9
     value = agent_steps / (total_ms_max / 1e3)
     traffic = profiled_traffic("sir_%s" % path)
+    # the step is issue-bound: its warp instructions (ncu) against the SMs'
+    # issue peak, 4 warp instructions per SM per cycle at the sampled clock
+    winst = profiled("sir_%s" % path, "warp_instructions_per_launch")
+    issue = None
+    if winst and clocks and clocks.get("sm_mhz"):
+        import torch
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        peak_issue = sms * 4 * clocks["sm_mhz"] * 1e6
+        issue = {"warp_instructions": winst, "achieved_per_s": winst / (step_ms / 1e3), "peak_per_s": peak_issue,
+                 "frac": winst / (step_ms / 1e3) / peak_issue, "sms": sms, "sm_mhz": clocks["sm_mhz"]}
     line = {
         "metric": "agent-steps/s (spatial SIR, 10M agents, 4096x4096 torus)",
         "value": value,
@@ -602,7 +617,7 @@ def gpu_arm(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "peak_kind": peak_kind, "traffic": traffic, "bytes_per_agent_step": b_alg,
                      "layout_bytes_per_agent_step": b_layout, "layout_frac": b_layout * n / (step_ms / 1e3) / 1e9 / hbm,
-                     "kernel_ms_median": step_ms},
+                     "kernel_ms_median": step_ms, "issue": issue},
         "cpu_baseline": None if only_sir else cpu_baseline(),
         "e2e": None if only_sir else {"value": e2e_val, "unit": "agent-steps/s",
                                       "h2d_bytes_per_step": e2e["h2d_bytes_per_step"],
