@@ -34,6 +34,11 @@ struct amb_table {
     uint32_t *err = nullptr;
     Lookback lb;
     int live_views = 0;
+    // where() scratch, made on first use: predicate words, per-tile counts
+    // and their exclusive scan
+    uint32_t *where_bits = nullptr;
+    int32_t *where_cnt = nullptr, *where_off = nullptr;
+    uint32_t *where_done = nullptr;  // blocks of the flag launch that finished (the last resets it)
 };
 
 struct amb_log {
@@ -148,71 +153,171 @@ __global__ void __launch_bounds__(kMapNT) map_col_kernel(D *__restrict__ d, cons
 }
 
 // ---------------------------------------------------------------- where ---
+// Order-preserving compaction in two streaming launches with no chain between
+// tiles.  (1) Every block reads a span of the column, 8 consecutive rows per
+// thread and span row (2 x 16 bytes of int32, 8 bytes of uint8), writes their
+// predicate bits as one byte to shared memory, so that the block's shared
+// bytes are the span's bitmap in row order, stores the bitmap and the count
+// of every write tile (kWhereTile rows); the last block to finish scans the
+// counts.  (2) One block per write tile turns its bitmap into ids, each warp
+// writing the selected rows of each 32-row word as one contiguous run.
 constexpr int kWhereNT = 512;
-constexpr int kWhereItems = 32;                          // per thread
-constexpr uint32_t kWhereTile = kWhereNT * kWhereItems;  // ids per tile
-constexpr int kWhereCtasPerSm = 3;                       // the staged ids take 64 KiB of shared memory per CTA
-static_assert(kWhereItems % 16 == 0 && kWhereItems <= 32, "predicate bits of a thread fit one word");
+constexpr uint32_t kWhereTile = 32u * kWhereNT;        // rows per write tile: one predicate word per thread
+constexpr uint32_t kWhereWords = kWhereTile / 32u;
+constexpr int kWhereRowsI32 = 8;   // span rows of an int32 column
+constexpr int kWhereRowsU8 = 16;   // span rows of a uint8 column
+template <class T>
+struct WhereSpan {
+    static constexpr uint32_t kRows = sizeof(T) == 4 ? kWhereRowsI32 : kWhereRowsU8;  // 8 column rows per thread each
+    static constexpr uint32_t kBytes = kRows * kWhereNT;          // bitmap bytes of a span
+    static constexpr uint32_t kItems = kBytes * 8u;               // column rows of a span
+    static constexpr uint32_t kTiles = kItems / kWhereTile;       // write tiles per span
+};
 
 template <int CMP, class T>
-__global__ void __launch_bounds__(kWhereNT) where_kernel(const T *__restrict__ c, uint32_t n, int64_t s,
-                                                          int32_t *__restrict__ ids, uint32_t *__restrict__ count,
-                                                          uint32_t n_tiles, unsigned long long *tickets,
-                                                          uint32_t parity, uint64_t *status, uint32_t epoch,
-                                                          uint32_t *err)
+__device__ __forceinline__ uint32_t where_bits8(const T *__restrict__ c, uint32_t i, uint32_t n, int64_t s)
 {
-    __shared__ uint32_t s_tile, s_prefix;
-    __shared__ uint32_t s_warp[kWhereNT / 32 + 1];
-    extern __shared__ int32_t s_ids[];  // kWhereTile (dynamic: the tile's ids in order)
-    const uint32_t tid = threadIdx.x;
-    if (blockIdx.x == 0 && tid == 0) tickets[parity ^ 1u] = 0ull;
-    for (;;) {
-        if (tid == 0) s_tile = (uint32_t)atomicAdd(&tickets[parity], 1ull);
-        __syncthreads();
-        const uint32_t tile = s_tile;
-        __syncthreads();
-        if (tile >= n_tiles) break;
-        const uint32_t i0 = tile * kWhereTile + tid * kWhereItems;
-        uint32_t bits = 0;
-        if (i0 + kWhereItems <= n) {
-            if constexpr (sizeof(T) == 4) {
+    uint32_t f = 0;
+    if (i + 8u <= n) {
+        if constexpr (sizeof(T) == 4) {
+            const int4 a = *reinterpret_cast<const int4 *>(c + i), b = *reinterpret_cast<const int4 *>(c + i + 4);
+            const int32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 #pragma unroll
-                for (int q = 0; q < kWhereItems / 4; ++q) {
-                    const int4 v = *reinterpret_cast<const int4 *>(c + i0 + 4 * q);
-                    bits |= (uint32_t)compare<CMP>(v.x, s) << (4 * q);
-                    bits |= (uint32_t)compare<CMP>(v.y, s) << (4 * q + 1);
-                    bits |= (uint32_t)compare<CMP>(v.z, s) << (4 * q + 2);
-                    bits |= (uint32_t)compare<CMP>(v.w, s) << (4 * q + 3);
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < kWhereItems / 16; ++q) {
-                    const uint4 v = *reinterpret_cast<const uint4 *>(c + i0 + 16 * q);
-                    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                    for (int k = 0; k < 16; ++k)
-                        bits |= (uint32_t)compare<CMP>((w[k >> 2] >> (8 * (k & 3))) & 0xFFu, s) << (16 * q + k);
-                }
-            }
+            for (int k = 0; k < 8; ++k) f |= (uint32_t)compare<CMP>((int64_t)v[k], s) << k;
         } else {
-            for (uint32_t k = 0; k < (uint32_t)kWhereItems; ++k)
-                if (i0 + k < n && compare<CMP>((int64_t)c[i0 + k], s)) bits |= 1u << k;
+            const uint2 a = *reinterpret_cast<const uint2 *>(c + i);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                f |= (uint32_t)compare<CMP>((int64_t)(((k < 4 ? a.x : a.y) >> (8 * (k & 3))) & 0xFFu), s) << k;
         }
-        uint32_t total;
-        const uint32_t ex = block_exclusive_scan<kWhereNT>(__popc(bits), s_warp, &total);
-        // stage the tile's ids in order, then write them out coalesced
-        uint32_t pos = ex;
-        for (uint32_t b = bits; b; b &= b - 1u) s_ids[pos++] = (int32_t)(i0 + __ffs(b) - 1);
-        if (tid < 32) {
-            const uint32_t pre = warp_lookback(status, tile, epoch, total, err);
-            if (tid == 0) s_prefix = pre;
-        }
-        __syncthreads();
-        const uint32_t pre = s_prefix;
-        for (uint32_t j = tid; j < total; j += kWhereNT) ids[pre + j] = s_ids[j];
-        if (tile == n_tiles - 1u && tid == 0) *count = pre + total;
-        __syncthreads();
+    } else {
+        for (uint32_t k = 0; k < 8u; ++k)
+            if (i + k < n && compare<CMP>((int64_t)c[i + k], s)) f |= 1u << k;
     }
+    return f;
+}
+
+template <int CMP, class T>
+__global__ void __launch_bounds__(kWhereNT) where_flags_kernel(const T *__restrict__ c, uint32_t n, int64_t s,
+                                                               uint32_t *__restrict__ bits, int32_t *__restrict__ cnt,
+                                                               int32_t *__restrict__ off, uint32_t n_tiles,
+                                                               uint32_t *__restrict__ done,
+                                                               uint32_t *__restrict__ count)
+{
+    using Sp = WhereSpan<T>;
+    __shared__ __align__(16) uint8_t s_map[Sp::kBytes];
+    __shared__ uint32_t s_sum[Sp::kTiles][kWhereNT / 32];
+    __shared__ uint32_t s_warp[kWhereNT / 32 + 1];
+    __shared__ bool s_last;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, wid = tid >> 5;
+    const uint32_t span0 = blockIdx.x * Sp::kItems;
+#pragma unroll 4
+    for (uint32_t r = 0; r < Sp::kRows; ++r)
+        s_map[r * kWhereNT + tid] = (uint8_t)where_bits8<CMP>(c, span0 + (r * kWhereNT + tid) * 8u, n, s);
+    __syncthreads();
+    // word tid + k kWhereNT of the span is word tid of its write tile k
+    const uint32_t *wmap = reinterpret_cast<const uint32_t *>(s_map);
+    const uint32_t tile0 = blockIdx.x * Sp::kTiles;
+#pragma unroll
+    for (uint32_t k = 0; k < Sp::kTiles; ++k) {
+        const uint32_t w = wmap[k * kWhereNT + tid];
+        if (tile0 + k < n_tiles) bits[(size_t)(tile0 + k) * kWhereWords + tid] = w;
+        uint32_t p = __popc(w);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+        if (lane == 0) s_sum[k][wid] = p;
+    }
+    __syncthreads();
+    if (tid < Sp::kTiles && tile0 + tid < n_tiles) {
+        uint32_t p = 0;
+        for (uint32_t w = 0; w < kWhereNT / 32; ++w) p += s_sum[tid][w];
+        cnt[tile0 + tid] = (int32_t)p;
+    }
+    // the last block to finish scans every tile's count
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(done, 1u) == gridDim.x - 1u);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // thread i scans a segment of `per` counts (all of them loaded at once
+    // when per <= kFast)
+    constexpr uint32_t kFast = 16;
+    const uint32_t per = (n_tiles + kWhereNT - 1u) / kWhereNT, j0 = min(tid * per, n_tiles), j1 = min(j0 + per, n_tiles);
+    uint32_t total;
+    if (per <= kFast) {
+        uint32_t val[kFast], part = 0;
+#pragma unroll
+        for (uint32_t q = 0; q < kFast; ++q) {
+            val[q] = (j0 + q < j1) ? (uint32_t)__ldcg(cnt + j0 + q) : 0u;
+            part += val[q];
+        }
+        uint32_t run = block_exclusive_scan<kWhereNT>(part, s_warp, &total);
+#pragma unroll
+        for (uint32_t q = 0; q < kFast; ++q) {
+            if (j0 + q < j1) off[j0 + q] = (int32_t)run;
+            run += val[q];
+        }
+    } else {
+        uint32_t part = 0;
+        for (uint32_t j = j0; j < j1; ++j) part += (uint32_t)__ldcg(cnt + j);
+        uint32_t run = block_exclusive_scan<kWhereNT>(part, s_warp, &total);
+        for (uint32_t j = j0; j < j1; ++j) {
+            off[j] = (int32_t)run;
+            run += (uint32_t)__ldcg(cnt + j);
+        }
+    }
+    if (tid == 0) {
+        off[n_tiles] = (int32_t)total;
+        *count = total;
+        *done = 0u;
+    }
+}
+
+// Ids of a write tile's selected rows from slot `first` on.  Thread t holds
+// word t (rows tile0 + 32 t ..) and its exclusive count `ex` within the tile;
+// the warp writes each of its 32 words' rows as one contiguous run.
+__device__ __forceinline__ void where_emit(uint32_t word, uint32_t ex, uint32_t first, uint32_t tile0,
+                                           int32_t *__restrict__ ids)
+{
+    const uint32_t lane = threadIdx.x & 31u, lt = (1u << lane) - 1u;
+    const uint32_t slot = first + ex, row0 = tile0 + threadIdx.x * 32u;
+#pragma unroll 4
+    for (int j = 0; j < 32; ++j) {
+        const uint32_t m = __shfl_sync(0xffffffffu, word, j);
+        if (m == 0u) continue;  // warp-uniform
+        const uint32_t p = __shfl_sync(0xffffffffu, slot, j), r0 = __shfl_sync(0xffffffffu, row0, j);
+        if ((m >> lane) & 1u) ids[p + __popc(m & lt)] = (int32_t)(r0 + lane);
+    }
+}
+
+__global__ void __launch_bounds__(kWhereNT) where_write_kernel(const uint32_t *__restrict__ bits,
+                                                               const int32_t *__restrict__ off,
+                                                               int32_t *__restrict__ ids)
+{
+    __shared__ uint32_t s_warp[kWhereNT / 32 + 1];
+    const uint32_t tile = blockIdx.x;
+    const uint32_t word = bits[(size_t)tile * kWhereWords + threadIdx.x];
+    uint32_t total;
+    const uint32_t ex = block_exclusive_scan<kWhereNT>(__popc(word), s_warp, &total);
+    where_emit(word, ex, (uint32_t)off[tile], tile * kWhereTile, ids);
+}
+
+// A table of one write tile: both steps in one block.
+template <int CMP, class T>
+__global__ void __launch_bounds__(kWhereNT) where_single_kernel(const T *__restrict__ c, uint32_t n, int64_t s,
+                                                                int32_t *__restrict__ ids, uint32_t *__restrict__ count)
+{
+    __shared__ __align__(16) uint8_t s_map[kWhereWords * 4u];
+    __shared__ uint32_t s_warp[kWhereNT / 32 + 1];
+    const uint32_t tid = threadIdx.x;
+    for (uint32_t b = tid; b < kWhereWords * 4u; b += kWhereNT) s_map[b] = (uint8_t)where_bits8<CMP>(c, b * 8u, n, s);
+    __syncthreads();
+    const uint32_t word = reinterpret_cast<const uint32_t *>(s_map)[tid];
+    uint32_t total;
+    const uint32_t ex = block_exclusive_scan<kWhereNT>(__popc(word), s_warp, &total);
+    where_emit(word, ex, 0u, 0u, ids);
+    if (tid == 0) *count = total;
 }
 
 // A view of a view: the listed ids (list order) whose value satisfies the
@@ -319,27 +424,61 @@ __device__ __forceinline__ void cas_update(uint32_t *word, F f, uint32_t *err)
     atomicOr(err, ERR_TIMEOUT);
 }
 
+// Updates through a view: every thread takes kViewU listed ids per pass
+// (list entries i0 + u kMapNT), so that their id loads, and then their column
+// loads, are independent requests in flight together.  Ids of a filtered view
+// are distinct, so all of a pass's reads can precede its writes; views that
+// may repeat ids update through atomics.
+constexpr int kViewU = 8;
+constexpr uint32_t kNoId = 0xFFFFFFFFu;
+
+__device__ __forceinline__ void load_ids(const int32_t *__restrict__ ids, uint32_t i0, uint32_t k, uint32_t id[kViewU])
+{
+#pragma unroll
+    for (int u = 0; u < kViewU; ++u) {
+        const uint32_t i = i0 + (uint32_t)u * kMapNT;
+        id[u] = i < k ? (uint32_t)ids[i] : kNoId;
+    }
+}
+
+template <int OP>
+__device__ __forceinline__ void atomic_update_i32(int32_t *c, uint32_t id, int32_t s, uint32_t *err)
+{
+    if constexpr (OP == AMB_OP_ADD) {
+        atomicAdd(reinterpret_cast<unsigned int *>(c + id), (unsigned int)s);
+    } else if constexpr (OP == AMB_OP_SUB) {
+        atomicSub(reinterpret_cast<unsigned int *>(c + id), (unsigned int)s);
+    } else if constexpr (OP == AMB_OP_MIN) {
+        atomicMin(c + id, s);
+    } else if constexpr (OP == AMB_OP_MAX) {
+        atomicMax(c + id, s);
+    } else {
+        cas_update(reinterpret_cast<uint32_t *>(c + id),
+                   [s](uint32_t v) { return (uint32_t)apply_i32<OP>((int32_t)v, s); }, err);
+    }
+}
+
 template <int OP, bool UNIQUE>
 __global__ void __launch_bounds__(kMapNT) view_map_i32_kernel(int32_t *__restrict__ c, const int32_t *__restrict__ ids,
                                                               const uint32_t *__restrict__ count, int32_t s,
                                                               uint32_t *err)
 {
     const uint32_t k = *count;
-    for (uint32_t i = blockIdx.x * kMapNT + threadIdx.x; i < k; i += gridDim.x * kMapNT) {
-        const uint32_t id = (uint32_t)ids[i];
+    for (uint32_t i0 = blockIdx.x * kMapNT * kViewU + threadIdx.x; i0 < k; i0 += gridDim.x * kMapNT * kViewU) {
+        uint32_t id[kViewU];
+        load_ids(ids, i0, k, id);
         if constexpr (UNIQUE || OP == AMB_OP_SET) {
-            c[id] = apply_i32<OP>(c[id], s);
-        } else if constexpr (OP == AMB_OP_ADD) {
-            atomicAdd(reinterpret_cast<unsigned int *>(c + id), (unsigned int)s);
-        } else if constexpr (OP == AMB_OP_SUB) {
-            atomicSub(reinterpret_cast<unsigned int *>(c + id), (unsigned int)s);
-        } else if constexpr (OP == AMB_OP_MIN) {
-            atomicMin(c + id, s);
-        } else if constexpr (OP == AMB_OP_MAX) {
-            atomicMax(c + id, s);
+            int32_t v[kViewU];
+#pragma unroll
+            for (int u = 0; u < kViewU; ++u)
+                if (id[u] != kNoId) v[u] = c[id[u]];
+#pragma unroll
+            for (int u = 0; u < kViewU; ++u)
+                if (id[u] != kNoId) c[id[u]] = apply_i32<OP>(v[u], s);
         } else {
-            cas_update(reinterpret_cast<uint32_t *>(c + id),
-                       [s](uint32_t v) { return (uint32_t)apply_i32<OP>((int32_t)v, s); }, err);
+#pragma unroll
+            for (int u = 0; u < kViewU; ++u)
+                if (id[u] != kNoId) atomic_update_i32<OP>(c, id[u], s, err);
         }
     }
 }
@@ -350,19 +489,30 @@ __global__ void __launch_bounds__(kMapNT) view_map_u8_kernel(uint8_t *__restrict
                                                              uint32_t *err)
 {
     const uint32_t k = *count;
-    for (uint32_t i = blockIdx.x * kMapNT + threadIdx.x; i < k; i += gridDim.x * kMapNT) {
-        const uint32_t id = (uint32_t)ids[i];
+    for (uint32_t i0 = blockIdx.x * kMapNT * kViewU + threadIdx.x; i0 < k; i0 += gridDim.x * kMapNT * kViewU) {
+        uint32_t id[kViewU];
+        load_ids(ids, i0, k, id);
         if constexpr (UNIQUE || OP == AMB_OP_SET) {
-            c[id] = apply_u8<OP>(c[id], s);
+            uint8_t v[kViewU];
+#pragma unroll
+            for (int u = 0; u < kViewU; ++u)
+                if (id[u] != kNoId) v[u] = c[id[u]];
+#pragma unroll
+            for (int u = 0; u < kViewU; ++u)
+                if (id[u] != kNoId) c[id[u]] = apply_u8<OP>(v[u], s);
         } else {
-            // the byte's aligned 32-bit word (columns are padded to 4 bytes)
-            const uint32_t sh = 8u * (id & 3u);
-            cas_update(reinterpret_cast<uint32_t *>(c + (id & ~3u)),
-                       [s, sh](uint32_t v) {
-                           const uint8_t r = apply_u8<OP>((uint8_t)(v >> sh), s);
-                           return (v & ~(0xFFu << sh)) | ((uint32_t)r << sh);
-                       },
-                       err);
+#pragma unroll
+            for (int u = 0; u < kViewU; ++u) {
+                if (id[u] == kNoId) continue;
+                // the byte's aligned 32-bit word (columns are padded to 4 bytes)
+                const uint32_t sh = 8u * (id[u] & 3u);
+                cas_update(reinterpret_cast<uint32_t *>(c + (id[u] & ~3u)),
+                           [s, sh](uint32_t v) {
+                               const uint8_t r = apply_u8<OP>((uint8_t)(v >> sh), s);
+                               return (v & ~(0xFFu << sh)) | ((uint32_t)r << sh);
+                           },
+                           err);
+            }
         }
     }
 }
@@ -376,13 +526,19 @@ __global__ void __launch_bounds__(kMapNT) view_draw_kernel(const int32_t *__rest
 {
     const uint32_t k = *count;
     if (blockIdx.x == 0 && threadIdx.x == 0) *out_count = k;
-    for (uint32_t i = blockIdx.x * kMapNT + threadIdx.x; i < k; i += gridDim.x * kMapNT) {
-        const uint32_t id = (uint32_t)ids[i];
-        const U4 u = philox(id, step, k0, k1);
-        const uint32_t w = word == 0 ? u.w0 : word == 1 ? u.w1 : word == 2 ? u.w2 : u.w3;
-        uint32_t r = below(w, exclude_self ? range - 1u : range);
-        if (exclude_self) r += (r >= id) ? 1u : 0u;
-        out[i] = (int32_t)r;
+    const uint32_t m = exclude_self ? range - 1u : range;
+    for (uint32_t i0 = blockIdx.x * kMapNT * kViewU + threadIdx.x; i0 < k; i0 += gridDim.x * kMapNT * kViewU) {
+        uint32_t id[kViewU];
+        load_ids(ids, i0, k, id);
+#pragma unroll
+        for (int u = 0; u < kViewU; ++u) {
+            if (id[u] == kNoId) continue;
+            const U4 q = philox(id[u], step, k0, k1);
+            const uint32_t w = word == 0 ? q.w0 : word == 1 ? q.w1 : word == 2 ? q.w2 : q.w3;
+            uint32_t r = below(w, m);
+            if (exclude_self) r += (r >= id[u]) ? 1u : 0u;
+            out[i0 + (uint32_t)u * kMapNT] = (int32_t)r;
+        }
     }
 }
 
@@ -590,16 +746,25 @@ amb_status launch_where_t(amb_table *t, const T *c, int cmp, int64_t s, amb_view
         return AMB_OK;
     }
     const uint32_t n_tiles = (n + kWhereTile - 1u) / kWhereTile;
-    AMB_TRY(t->lb.ensure(n_tiles, st));
-    uint32_t parity, epoch;
-    t->lb.next(&parity, &epoch);
-    const unsigned g = std::min<uint32_t>(n_tiles, 152u * kWhereCtasPerSm);
-    constexpr size_t smem = (size_t)kWhereTile * sizeof(int32_t);
-#define WHERE_CASE(C)                                                                                              \
-    case C:                                                                                                        \
-        AMB_TRY_CUDA(cudaFuncSetAttribute(where_kernel<C, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-        where_kernel<C, T><<<g, kWhereNT, smem, st>>>(c, n, s, v->ids, v->count, n_tiles, t->lb.tickets, parity,     \
-                                                      t->lb.status, epoch, t->err);                                 \
+    const uint32_t n_spans = (n + WhereSpan<T>::kItems - 1u) / WhereSpan<T>::kItems;
+    if (n_tiles > 1u && !t->where_bits) {
+        AMB_TRY(dalloc(&t->where_bits, (size_t)n_tiles * kWhereWords, st));
+        AMB_TRY(dalloc(&t->where_cnt, n_tiles, st));
+        AMB_TRY(dalloc(&t->where_off, (size_t)n_tiles + 1u, st));
+        AMB_TRY(dalloc(&t->where_done, 1, st));
+        AMB_TRY_CUDA(cudaMemsetAsync(t->where_done, 0, sizeof(uint32_t), st));
+    }
+#define WHERE_CASE(C)                                                                                            \
+    case C:                                                                                                      \
+        if (n_tiles == 1u) {                                                                                     \
+            where_single_kernel<C, T><<<1, kWhereNT, 0, st>>>(c, n, s, v->ids, v->count);                        \
+        } else {                                                                                                 \
+            where_flags_kernel<C, T><<<n_spans, kWhereNT, 0, st>>>(c, n, s, t->where_bits, t->where_cnt,         \
+                                                                   t->where_off, n_tiles, t->where_done,        \
+                                                                   v->count);                                    \
+            AMB_TRY_CUDA(cudaGetLastError());                                                                    \
+            where_write_kernel<<<n_tiles, kWhereNT, 0, st>>>(t->where_bits, t->where_off, v->ids);              \
+        }                                                                                                        \
         break;
     switch (cmp) {
         WHERE_CASE(AMB_CMP_EQ)
@@ -621,7 +786,7 @@ amb_status launch_view_map_t(amb_view *v, const Column &col, int op, int64_t s)
     amb_table *t = v->t;
     cudaStream_t st = t->stream;
     if (v->capacity == 0) return AMB_OK;
-    const unsigned g = map_grid(v->capacity);
+    const unsigned g = map_grid(((uint64_t)v->capacity + kViewU - 1u) / kViewU);
 #define VM_CASE(K, O, val) \
     case O: K<O, UNIQUE><<<g, kMapNT, 0, st>>>(c, v->ids, v->count, val, t->err); break;
     if (col.dtype == AMB_DT_I32) {
@@ -734,6 +899,10 @@ amb_status amb_table_destroy(amb_table *t)
     if (t->live_views) return fail(AMB_EBUSY, "%d views of this table are still alive", t->live_views);
     for (Column &c : t->cols) dfree(c.ptr, t->stream);
     dfree(t->err, t->stream);
+    dfree(t->where_bits, t->stream);
+    dfree(t->where_cnt, t->stream);
+    dfree(t->where_off, t->stream);
+    dfree(t->where_done, t->stream);
     t->lb.release(t->stream);
     cudaStreamSynchronize(t->stream);
     delete t;
@@ -911,7 +1080,7 @@ amb_status amb_view_draw(amb_view *v, uint64_t seed, uint32_t replicate, uint32_
     amb_view *r = nullptr;
     AMB_TRY(new_view(t, v->capacity, false, &r));
     if (v->capacity) {
-        view_draw_kernel<<<map_grid(v->capacity), kMapNT, 0, t->stream>>>(v->ids, v->count, r->ids, r->count, (uint32_t)seed,
+        view_draw_kernel<<<map_grid(((uint64_t)v->capacity + kViewU - 1u) / kViewU), kMapNT, 0, t->stream>>>(v->ids, v->count, r->ids, r->count, (uint32_t)seed,
                                                                           replicate, step, word, range, exclude_self);
     } else {
         cudaMemsetAsync(r->count, 0, sizeof(uint32_t), t->stream);
