@@ -13,7 +13,9 @@ from paper_2601_16292_gb300 import amb
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-SIZES = [0, 1, 5, 17, 4095, 4099, 16383, 16384, 16385, 3 * 16384 + 13, (1 << 20) + 7]
+# around the 16,384-row write tiles and the 32,768 / 65,536-row spans of `where`
+SIZES = [0, 1, 5, 17, 4095, 4099, 16383, 16384, 16385, 32767, 32768, 32769, 3 * 16384 + 13, 65535, 65537,
+         2 * 65536 + 1, (1 << 20) + 7]
 RNG = np.random.default_rng(11)
 
 
@@ -107,6 +109,26 @@ def test_updates_through_views(stream, dtype, op, s):
     with t.at(dev_ids) as v:
         v.scatter_add("c", 1)
     oracle.view_map(want, dev_ids.cpu().numpy(), "add", 1)
+    assert np.array_equal(t.read("c").numpy(), want)
+    t.close()
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.uint8])
+@pytest.mark.parametrize("op,s", [("add", 3), ("mul", 3), ("set", 9), ("max", 200)])
+def test_updates_through_views_large(stream, dtype, op, s):
+    # lists longer than one pass of the update kernels (8 ids per thread)
+    n = (1 << 20) + 5
+    col = _rand(dtype, n)
+    t = _table(n, stream, {"c": col})
+    want = col.copy()
+    with t.where("c", ">", 50) as v:
+        f_ids = v.ids()
+        v.map("c", op, s)
+    oracle.view_map(want, f_ids, op, s)
+    ids = RNG.integers(0, n, 3 * n + 1).astype(np.int32)
+    with t.at(ids) as v:
+        v.map("c", op, s)
+    oracle.view_map(want, ids, op, s)
     assert np.array_equal(t.read("c").numpy(), want)
     t.close()
 
