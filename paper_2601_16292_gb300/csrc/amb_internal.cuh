@@ -6,7 +6,20 @@
 
 #include "amb_common.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace amb {
+
+// NVTX range over one library call (header-only NVTX v3: a no-op unless a
+// profiler such as Nsight Compute or Systems is attached).
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
+#define AMB_TRACE(name) ::amb::TraceRange amb_trace_range_(name)
+
 
 // The library's stream-ordered memory pool on the current device: freed
 // blocks stay cached in the pool (release threshold: never), so repeated

@@ -247,6 +247,7 @@ extern "C" {
 
 amb_status amb_batch_create(const amb_job *jobs, size_t n, void *cuda_stream, amb_batch **out)
 {
+    AMB_TRACE("amb_batch_create");
     if (!out || (!jobs && n)) return fail(AMB_EINVAL, "null pointer");
     *out = nullptr;
     for (size_t i = 0; i < n; ++i)
@@ -267,6 +268,7 @@ amb_status amb_batch_create(const amb_job *jobs, size_t n, void *cuda_stream, am
 
 amb_status amb_batch_run(amb_batch *b, const amb_tune *tune, double *ms_out)
 {
+    AMB_TRACE("amb_batch_run");
     if (!b) return fail(AMB_EINVAL, "null batch");
     if (b->ran) return fail(AMB_EINVAL, "a batch runs once");
     cudaStream_t s = b->stream;

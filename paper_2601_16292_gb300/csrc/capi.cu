@@ -360,6 +360,7 @@ extern "C" {
 amb_status amb_create(amb_model model, const amb_params *p, uint64_t seed, uint32_t replicate, void *cuda_stream,
                       amb_pop **out)
 {
+    AMB_TRACE("amb_create");
     if (!p || !out) return fail(AMB_EINVAL, "null pointer");
     *out = nullptr;
     AMB_TRY(check_params(model, p, seed));
@@ -476,6 +477,7 @@ amb_status amb_synchronize(amb_pop *pop)
 
 amb_status amb_step(amb_pop *pop, uint32_t k)
 {
+    AMB_TRACE("amb_step");
     if (!pop) return fail(AMB_EINVAL, "null population");
     AMB_TRY(band_sync_records(pop));
     if (k == 0) return AMB_OK;
@@ -498,6 +500,7 @@ amb_status amb_step(amb_pop *pop, uint32_t k)
 
 amb_status amb_set_step(amb_pop *pop, uint64_t t)
 {
+    AMB_TRACE("amb_set_step");
     if (!pop) return fail(AMB_EINVAL, "null population");
     if (t >= (uint64_t)kInitStep) return fail(AMB_EINVAL, "step index must be < 2^32 - 1");
     AMB_TRY(device_error(pop));
@@ -531,6 +534,7 @@ amb_status amb_set_step(amb_pop *pop, uint64_t t)
 
 amb_status amb_write_column(amb_pop *pop, amb_col col, const void *src, size_t n, int src_on_device)
 {
+    AMB_TRACE("amb_write_column");
     if (!pop || (!src && n)) return fail(AMB_EINVAL, "null pointer");
     if (n != pop->p.n) return fail(AMB_EINVAL, "column length %zu != n = %u", n, pop->p.n);
     if (is_continuous(pop)) {
@@ -618,6 +622,7 @@ amb_status amb_write_column(amb_pop *pop, amb_col col, const void *src, size_t n
 
 amb_status amb_read_column(amb_pop *pop, amb_col col, void *dst, size_t n, int dst_on_device)
 {
+    AMB_TRACE("amb_read_column");
     if (!pop || (!dst && n)) return fail(AMB_EINVAL, "null pointer");
     AMB_TRY(band_sync_records(pop));
     if (n != pop->p.n) return fail(AMB_EINVAL, "column length %zu != n = %u", n, pop->p.n);
@@ -707,6 +712,7 @@ amb_status amb_read_index(amb_pop *pop, int32_t *start, int32_t *ids, int dst_on
 
 amb_status amb_occupancy(amb_pop *pop, int32_t *occ, int dst_on_device)
 {
+    AMB_TRACE("amb_occupancy");
     if (!pop || !occ) return fail(AMB_EINVAL, "null pointer");
     AMB_TRY(band_sync_records(pop));
     if (pop->model == AMB_WEALTH) return fail(AMB_EINVAL, "the wealth model has no grid");
@@ -725,6 +731,7 @@ amb_status amb_occupancy(amb_pop *pop, int32_t *occ, int dst_on_device)
 
 amb_status amb_invariants(amb_pop *pop, amb_invariant_report *out)
 {
+    AMB_TRACE("amb_invariants");
     if (!pop || !out) return fail(AMB_EINVAL, "null pointer");
     AMB_TRY(band_sync_records(pop));
     AMB_TRY(device_error(pop));
@@ -805,6 +812,7 @@ amb_status amb_invariants(amb_pop *pop, amb_invariant_report *out)
 
 amb_status amb_stats_compute(amb_pop *pop, amb_stats *out, int64_t *hist, size_t hist_cap, size_t *hist_len)
 {
+    AMB_TRACE("amb_stats_compute");
     if (!pop || !out) return fail(AMB_EINVAL, "null pointer");
     AMB_TRY(band_sync_records(pop));
     AMB_TRY(device_error(pop));
@@ -968,6 +976,7 @@ amb_status amb_selfcheck_wait_timeout(void *cuda_stream, double *waited_s)
 amb_status amb_cell_index(const int32_t *x, const int32_t *y, uint32_t n, uint32_t L, int32_t *start, int32_t *ids,
                           void *cuda_stream, int sync)
 {
+    AMB_TRACE("amb_cell_index");
     if ((!x || !y || !ids) && n) return fail(AMB_EINVAL, "null pointer");
     if (!start) return fail(AMB_EINVAL, "null pointer");
     if (L < 1 || (uint64_t)L * L >= 0x80000000ull) return fail(AMB_EINVAL, "need 1 <= L and L*L < 2^31");

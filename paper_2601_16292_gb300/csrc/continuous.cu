@@ -549,6 +549,7 @@ using namespace amb;
 extern "C" amb_status amb_create_continuous(amb_model model, const amb_cparams *p, uint64_t seed, uint32_t replicate,
                                             void *cuda_stream, amb_pop **out)
 {
+    AMB_TRACE("amb_create_continuous");
     if (!p || !out) return fail(AMB_EINVAL, "null pointer");
     *out = nullptr;
     AMB_TRY(check_cparams(model, p, seed));

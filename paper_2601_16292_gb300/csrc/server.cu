@@ -202,6 +202,7 @@ void worker_loop(amb_server *S)
         if (S->active.empty()) continue;
 
         // one iteration: every active job advances by up to `chunk` steps
+        AMB_TRACE("amb_server_iteration");
         const double t0 = S->now();
         std::vector<amb_pop *> pops;
         std::vector<uint32_t> ks;
@@ -297,6 +298,7 @@ amb_status amb_server_create(const amb_server_config *cfg, void *cuda_stream, am
 
 amb_status amb_server_submit(amb_server *S, const amb_job *job, int keep_columns, uint64_t *ticket)
 {
+    AMB_TRACE("amb_server_submit");
     if (!S || !job || !ticket) return fail(AMB_EINVAL, "null pointer");
     if (job->model == AMB_SIR && job->params.variant == AMB_SIR_GENERIC)
         return fail(AMB_EINVAL, "the server runs SIR on the band path");
@@ -369,6 +371,7 @@ amb_status amb_server_counts(amb_server *S, uint64_t ticket, int64_t *out, size_
 
 amb_status amb_server_read_column(amb_server *S, uint64_t ticket, amb_col col, void *dst, size_t n)
 {
+    AMB_TRACE("amb_server_read_column");
     if (!S || (!dst && n)) return fail(AMB_EINVAL, "null pointer");
     std::lock_guard<std::mutex> lk(S->mu);
     ServerJob *j = find_locked(S, ticket);

@@ -967,6 +967,7 @@ amb_status amb_table_rows(amb_table *t, uint32_t *n)
 
 amb_status amb_table_write(amb_table *t, int col, const void *src, size_t n, int src_on_device)
 {
+    AMB_TRACE("amb_table_write");
     Column *c = nullptr;
     AMB_TRY(get_col(t, col, &c));
     if (n != t->n) return fail(AMB_EINVAL, "column length %zu != n = %u", n, t->n);
@@ -981,6 +982,7 @@ amb_status amb_table_write(amb_table *t, int col, const void *src, size_t n, int
 
 amb_status amb_table_read(amb_table *t, int col, void *dst, size_t n, int dst_on_device)
 {
+    AMB_TRACE("amb_table_read");
     Column *c = nullptr;
     AMB_TRY(get_col(t, col, &c));
     if (n != t->n) return fail(AMB_EINVAL, "column length %zu != n = %u", n, t->n);
@@ -996,6 +998,7 @@ amb_status amb_table_read(amb_table *t, int col, void *dst, size_t n, int dst_on
 
 amb_status amb_table_map(amb_table *t, int col, amb_op op, int64_t scalar)
 {
+    AMB_TRACE("amb_table_map");
     Column *c = nullptr;
     AMB_TRY(get_col(t, col, &c));
     return launch_map(*c, t->n, op, scalar, t->stream);
@@ -1003,6 +1006,7 @@ amb_status amb_table_map(amb_table *t, int col, amb_op op, int64_t scalar)
 
 amb_status amb_table_map_col(amb_table *t, int dst, amb_op op, int src)
 {
+    AMB_TRACE("amb_table_map_col");
     Column *d = nullptr, *s = nullptr;
     AMB_TRY(get_col(t, dst, &d));
     AMB_TRY(get_col(t, src, &s));
@@ -1018,6 +1022,7 @@ amb_status amb_table_map_col(amb_table *t, int dst, amb_op op, int src)
 
 amb_status amb_table_where(amb_table *t, int col, amb_cmp cmp, int64_t scalar, amb_view **out)
 {
+    AMB_TRACE("amb_table_where");
     if (!out) return fail(AMB_EINVAL, "null pointer");
     *out = nullptr;
     Column *c = nullptr;
@@ -1038,6 +1043,7 @@ amb_status amb_table_where(amb_table *t, int col, amb_cmp cmp, int64_t scalar, a
 
 amb_status amb_view_from_ids(amb_table *t, const int32_t *ids, size_t k, int ids_on_device, amb_view **out)
 {
+    AMB_TRACE("amb_view_from_ids");
     if (!t || !out || (!ids && k)) return fail(AMB_EINVAL, "null pointer");
     *out = nullptr;
     if (k > 0x7FFFFFFFu) return fail(AMB_EINVAL, "too many ids");
@@ -1070,6 +1076,7 @@ amb_status amb_view_from_ids(amb_table *t, const int32_t *ids, size_t k, int ids
 amb_status amb_view_draw(amb_view *v, uint64_t seed, uint32_t replicate, uint32_t step, uint32_t word, uint32_t range,
                          int exclude_self, amb_view **out)
 {
+    AMB_TRACE("amb_view_draw");
     if (!v || !out) return fail(AMB_EINVAL, "null pointer");
     *out = nullptr;
     if (seed > 0xFFFFFFFFull) return fail(AMB_EINVAL, "seed must be < 2^32");
@@ -1095,6 +1102,7 @@ amb_status amb_view_draw(amb_view *v, uint64_t seed, uint32_t replicate, uint32_
 
 amb_status amb_view_where(amb_view *v, int col, amb_cmp cmp, int64_t scalar, amb_view **out)
 {
+    AMB_TRACE("amb_view_where");
     if (!v || !out) return fail(AMB_EINVAL, "null pointer");
     *out = nullptr;
     amb_table *t = v->t;
@@ -1153,6 +1161,7 @@ amb_status amb_view_where(amb_view *v, int col, amb_cmp cmp, int64_t scalar, amb
 
 amb_status amb_view_scatter_add_values(amb_view *v, int col, const int32_t *values, size_t n_values)
 {
+    AMB_TRACE("amb_view_scatter_add_values");
     if (!v || (!values && n_values)) return fail(AMB_EINVAL, "null pointer");
     amb_table *t = v->t;
     Column *c = nullptr;
@@ -1172,6 +1181,7 @@ amb_status amb_view_scatter_add_values(amb_view *v, int col, const int32_t *valu
 
 amb_status amb_view_map(amb_view *v, int col, amb_op op, int64_t scalar)
 {
+    AMB_TRACE("amb_view_map");
     if (!v) return fail(AMB_EINVAL, "null view");
     Column *c = nullptr;
     AMB_TRY(get_col(v->t, col, &c));
@@ -1195,6 +1205,7 @@ amb_status amb_view_count(amb_view *v, size_t *count)
 
 amb_status amb_view_ids(amb_view *v, int32_t *dst, size_t cap, int dst_on_device, size_t *count)
 {
+    AMB_TRACE("amb_view_ids");
     if (!v || (!dst && cap)) return fail(AMB_EINVAL, "null pointer");
     size_t k = 0;
     AMB_TRY(amb_view_count(v, &k));
@@ -1287,6 +1298,7 @@ amb_status amb_log_pending(amb_log *l, size_t *k)
 
 amb_status amb_log_flush(amb_log *l)
 {
+    AMB_TRACE("amb_log_flush");
     if (!l) return fail(AMB_EINVAL, "null log");
     amb_table *t = l->t;
     cudaStream_t s = t->stream;
@@ -1329,6 +1341,7 @@ amb_status amb_log_destroy(amb_log *l)
 amb_status amb_table_grid_walk(amb_table *t, const int *cols, uint32_t d, const uint32_t *sizes, int moore, int torus,
                                uint64_t seed, uint32_t replicate, uint32_t step, uint32_t steps)
 {
+    AMB_TRACE("amb_table_grid_walk");
     if (!t || !cols || !sizes) return fail(AMB_EINVAL, "null pointer");
     if (d < 1 || d > 4) return fail(AMB_EINVAL, "grids have 1 to 4 dimensions");
     if (seed > 0xFFFFFFFFull) return fail(AMB_EINVAL, "seed must be < 2^32");
