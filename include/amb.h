@@ -186,9 +186,14 @@ amb_status amb_counts(amb_pop *pop, int64_t *out, size_t cap_rows, size_t *rows_
  * Synchronises. */
 amb_status amb_counts_range(amb_pop *pop, uint64_t first, size_t n_rows, int64_t *out);
 
-/* As amb_counts_range, but asynchronous: the copy is queued on the
- * population's stream and the call returns at once (use page-locked host
- * memory for a truly asynchronous copy; read out after amb_synchronize). */
+/* As amb_counts_range, but asynchronous: the copy runs on a side stream of
+ * the library, ordered after the work queued so far on the population's
+ * stream, and the call returns at once, so later steps do not wait for the
+ * copy.  The rows in `out` are final once amb_synchronize (or any call that
+ * synchronises the population, or amb_destroy) has returned; the stream
+ * itself does not cover the copy.  Use page-locked host memory for a truly
+ * asynchronous copy.  Errors: AMB_EINVAL for rows not recorded yet,
+ * AMB_ECUDA if the side stream cannot be created. */
 amb_status amb_counts_async(amb_pop *pop, uint64_t first, size_t n_rows, int64_t *out);
 
 /*

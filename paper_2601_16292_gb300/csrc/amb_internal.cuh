@@ -230,6 +230,13 @@ struct amb_pop {
 
     // per-step counts: rows of 4 int64
     int64_t *series = nullptr;
+    // amb_counts_async copies run on a side stream after an event recorded on
+    // `stream`, so later steps do not wait for them; `stream` waits for
+    // ev_copied before anything that synchronises the population or frees
+    // `series`
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_ready = nullptr, ev_copied = nullptr;
+    bool copies_pending = false;
     size_t series_cap = 0;
 
     // continuous-space models: float positions, days infected, and the

@@ -134,8 +134,20 @@ __global__ void range_check_u8_kernel(const uint8_t *__restrict__ v, uint32_t n,
 }
 
 // ------------------------------------------------------------ helpers ---
+// Orders the population's stream after the counts copies queued on the side
+// stream (the last copy event covers the earlier ones: the side stream is in
+// order).
+static amb_status join_copies(amb_pop *pop)
+{
+    if (!pop->copies_pending) return AMB_OK;
+    AMB_TRY_CUDA(cudaStreamWaitEvent(pop->stream, pop->ev_copied, 0));
+    pop->copies_pending = false;
+    return AMB_OK;
+}
+
 static amb_status device_error(amb_pop *pop)
 {
+    AMB_TRY(join_copies(pop));
     uint32_t h = 0;
     AMB_TRY_CUDA(cudaMemcpyAsync(&h, pop->err, sizeof(h), cudaMemcpyDeviceToHost, pop->stream));
     AMB_TRY_CUDA(cudaStreamSynchronize(pop->stream));
@@ -155,6 +167,7 @@ amb_status ensure_series(amb_pop *pop, uint64_t rows)
     if (pop->series && pop->t)
         AMB_TRY_CUDA(cudaMemcpyAsync(ns, pop->series, (size_t)pop->t * 4u * sizeof(int64_t), cudaMemcpyDeviceToDevice,
                                      pop->stream));
+    AMB_TRY(join_copies(pop));  // pending copies still read the old rows
     dfree(pop->series, pop->stream);
     pop->series = ns;
     pop->series_cap = cap;
@@ -237,6 +250,7 @@ static amb_status build_index(amb_pop *pop)
 static void release(amb_pop *pop)
 {
     cudaStream_t s = pop->stream;
+    join_copies(pop);
     dfree(pop->w, s);
     dfree(pop->credit, s);
     dfree(pop->x, s);
@@ -462,6 +476,9 @@ amb_status amb_destroy(amb_pop *pop)
     cudaStream_t s = pop->stream;
     release(pop);
     cudaError_t e = cudaStreamSynchronize(s);
+    if (pop->copy_stream) cudaStreamDestroy(pop->copy_stream);
+    if (pop->ev_ready) cudaEventDestroy(pop->ev_ready);
+    if (pop->ev_copied) cudaEventDestroy(pop->ev_copied);
     delete pop;
     if (e != cudaSuccess) return fail(AMB_ECUDA, "cudaStreamSynchronize: %s", cudaGetErrorString(e));
     return AMB_OK;
@@ -676,9 +693,27 @@ amb_status amb_counts_async(amb_pop *pop, uint64_t first, size_t n_rows, int64_t
     if (!pop || (!out && n_rows)) return fail(AMB_EINVAL, "null pointer");
     if (first + n_rows > pop->t) return fail(AMB_EINVAL, "rows %llu..%llu not recorded yet", (unsigned long long)first,
                                              (unsigned long long)(first + n_rows));
-    if (n_rows)
-        AMB_TRY_CUDA(cudaMemcpyAsync(out, pop->series + first * 4u, n_rows * 4u * sizeof(int64_t), cudaMemcpyDefault,
-                                     pop->stream));
+    if (n_rows == 0) return AMB_OK;
+    if (!pop->copy_stream) {
+        cudaStream_t cs = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e0, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess) {
+            if (cs) cudaStreamDestroy(cs);
+            if (e0) cudaEventDestroy(e0);
+            return fail(AMB_ECUDA, "side stream for asynchronous counts could not be created");
+        }
+        pop->copy_stream = cs;
+        pop->ev_ready = e0;
+        pop->ev_copied = e1;
+    }
+    AMB_TRY_CUDA(cudaEventRecord(pop->ev_ready, pop->stream));
+    AMB_TRY_CUDA(cudaStreamWaitEvent(pop->copy_stream, pop->ev_ready, 0));
+    AMB_TRY_CUDA(cudaMemcpyAsync(out, pop->series + first * 4u, n_rows * 4u * sizeof(int64_t), cudaMemcpyDefault,
+                                 pop->copy_stream));
+    AMB_TRY_CUDA(cudaEventRecord(pop->ev_copied, pop->copy_stream));
+    pop->copies_pending = true;
     return AMB_OK;
 }
 

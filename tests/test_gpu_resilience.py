@@ -116,3 +116,35 @@ def test_async_counts_equal_counts(stream):
     with pytest.raises(amb.AmbError):
         amb.amb_counts_async(p.handle, 20, 1, rows[0])
     p.close()
+
+
+@pytest.mark.parametrize("model", ["sir", "walk", "wealth"])
+def test_async_counts_across_series_growth_resume_and_destroy(stream, model):
+    # copies still queued when the count series is reallocated (it grows past
+    # 64 and 128 rows), when the step counter is moved back, and at destroy;
+    # a twin population run the same way gives the expected rows
+    kw = dict(L=120) if model != "wealth" else {}
+    if model == "sir":
+        kw.update(beta=0.3, gamma=0.05, n0=20)
+    p = amb.Population(model, 8_000, seed=4, stream=stream, **kw)
+    q = amb.Population(model, 8_000, seed=4, stream=stream, **kw)
+    steps = 200
+    rows = torch.zeros((steps, 4), dtype=torch.int64, pin_memory=True)
+    for k in range(steps):
+        p.step(1)
+        amb.amb_counts_async(p.handle, k, 1, rows[k])
+    q.step(steps)
+    want = q.counts()
+    tail = torch.zeros((10, 4), dtype=torch.int64, pin_memory=True)
+    amb.amb_counts_async(p.handle, steps - 10, 10, tail)
+    p.set_step(150)  # synchronises: the queued copies finish before rows are rewritten
+    assert np.array_equal(rows.numpy(), want)
+    assert np.array_equal(tail.numpy(), want[-10:])
+    q.set_step(150)
+    p.step(1)
+    q.step(1)
+    last = torch.zeros((1, 4), dtype=torch.int64, pin_memory=True)
+    amb.amb_counts_async(p.handle, 150, 1, last)
+    p.close()  # destroy with the copy queued: it completes first
+    assert np.array_equal(last.numpy(), q.counts()[150:151])
+    q.close()
