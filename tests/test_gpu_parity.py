@@ -261,6 +261,32 @@ def test_sir_ten_million_agents_prefix():
     g.close()
 
 
+def test_sir_ten_million_agents_benchmark_length():
+    # the benchmark's workload and launch configuration, all 300 steps: the
+    # oracle cannot follow that far, so the checks are properties that hold at
+    # any size (counts, conservation, monotone R, new infections bounded by
+    # the susceptibles) and equality with the same run cut into other chunks
+    n, L, steps = 10_000_000, 4096, 300
+    kw = dict(seed=2, L=L, beta=0.05, gamma=0.02, n0=10_000)
+    a = amb.Population("sir", n, **kw)
+    b = amb.Population("sir", n, **kw)
+    a.step(steps)
+    for k in (1, 6, 93, 200):
+        b.step(k)
+    c = a.counts()
+    assert c.shape == (steps, 4)
+    assert np.all(c[:, :3].sum(axis=1) == n)
+    assert np.all(np.diff(c[:, 2]) >= 0) and c[0, 2] >= 0
+    s_prev = np.concatenate([[n - 10_000], c[:-1, 0]])
+    assert np.all(c[:, 3] == s_prev - c[:, 0])  # every new infection leaves S
+    assert np.array_equal(c, b.counts())
+    for name in ("x", "y", "state"):
+        assert torch.equal(a.column(name), b.column(name)), name
+    assert a.invariants()["ok"] == 1
+    a.close()
+    b.close()
+
+
 def test_write_column_rejects_out_of_range():
     g = amb.Population("sir", 100, seed=1, L=10, beta=0.1, gamma=0.1, n0=1)
     bad = np.zeros(100, np.uint8)
