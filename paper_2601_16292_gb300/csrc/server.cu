@@ -103,6 +103,9 @@ extern "C" amb_status amb_job_bytes(const amb_job *job, size_t *resident, size_t
         t = 13 * n + 8 * C;
         break;
     }
+    case AMB_CWALK:
+    case AMB_CSIR:  // rejected by check_params: continuous models are not batched or served
+        return fail(AMB_EINVAL, "continuous-space models are not served");
     }
     *resident = (size_t)r + kPoolSlack;
     *transient = (size_t)t;
