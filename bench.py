@@ -455,7 +455,54 @@ def views_bench(amb, torch, stream, hbm, n=100_000_000, reps=5):
     out["draw"] = {"ms": ms, "bytes": 8 * k}
     sv.close()
     v.close()
+    # buffered writes: 10M records on random rows (repeats included) of the
+    # 100M-row column, applied by one flush (last record per row wins); bytes:
+    # each record's row id, column index and value read once, each written row
+    # written once
+    n_rec = 10_000_000
+    rec_ids = torch.from_numpy(rng.integers(0, n, n_rec, dtype=np.int32)).cuda()
+    rec_vals = torch.from_numpy(rng.integers(-5, 5, n_rec, dtype=np.int64)).cuda()
+    rows_written = int(np.unique(rec_ids.cpu().numpy()).size)
+    log = t.log(n_rec)
+    log.record("c", rec_ids, rec_vals)
+    log.flush()  # first flush allocates the winner words
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        log.record("c", rec_ids, rec_vals)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        log.flush()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    out["log_flush_10M_records"] = {"ms": sorted(ms)[len(ms) // 2], "bytes": 16 * n_rec + 4 * rows_written,
+                                    "records": n_rec, "rows_written": rows_written}
+    log.close()
     t.close()
+    # grid walks (k steps fused in registers): 10M agents, 3-D von Neumann in a
+    # bounded 256 x 256 x 160 box and 2-D Moore on a 4096^2 torus, 50 steps;
+    # bytes: every coordinate read and written once per call
+    ng, gsteps = 10_000_000, 50
+    tg = amb.Table(ng, stream)
+    for name, size in (("gx", 256), ("gy", 256), ("gz", 160)):
+        tg.add_column(name, "i32", fill=0)
+        tg.write(name, rng.integers(0, size, ng, dtype=np.int32))
+    for key, cols, sizes, moore, torus in (("grid_walk_3d_vn_bounded", ["gx", "gy", "gz"], [256, 256, 160], False, False),
+                                           ("grid_walk_2d_moore_torus", ["gx", "gy"], [4096, 4096], True, True)):
+        tg.grid_walk(cols, sizes, moore=moore, torus=torus, seed=1, step=0, steps=2)
+        torch.cuda.synchronize()
+        ms = []
+        for r in range(reps):
+            e0.record(stream)
+            tg.grid_walk(cols, sizes, moore=moore, torus=torus, seed=1, step=2 + r * gsteps, steps=gsteps)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        m = sorted(ms)[len(ms) // 2]
+        out[key] = {"ms": m, "bytes": 8 * len(cols) * ng, "agent_steps_per_s": ng * gsteps / (m / 1e3),
+                    "bound": "integer multiply (one Philox per agent-step)"}
+    tg.close()
     for r in out.values():
         r["gbs"] = r["bytes"] / (r["ms"] / 1e3) / 1e9
         r["frac"] = r["gbs"] / hbm

@@ -611,12 +611,25 @@ __device__ __forceinline__ int32_t wrap_coord(int32_t v, int32_t o, uint32_t siz
     return (int32_t)s;
 }
 
-__global__ void grid_walk_kernel(GridWalkArgs a, uint32_t *err)
+// m -> (m / v, m % v) for a per-dimension neighbour count v in {1, 2, 3}
+__device__ __forceinline__ uint32_t divmod123(uint32_t &m, uint32_t v)
+{
+    const uint32_t q3 = m / 3u, q2 = m >> 1;
+    const uint32_t r = v == 3u ? m - 3u * q3 : v == 2u ? (m & 1u) : 0u;
+    m = v == 3u ? q3 : v == 2u ? q2 : m;
+    return r;
+}
+
+// Dimension count and neighbourhood are template arguments, so the
+// per-dimension loops unroll and a torus divides by the constant 3.
+template <uint32_t D, bool MOORE, bool TORUS>
+__global__ void __launch_bounds__(256) grid_walk_kernel(GridWalkArgs a, uint32_t *err)
 {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
-        int32_t c[4] = {0, 0, 0, 0};
+        int32_t c[D];
         bool ok = true;
-        for (uint32_t q = 0; q < a.d; ++q) {
+#pragma unroll
+        for (uint32_t q = 0; q < D; ++q) {
             c[q] = a.c[q][i];
             ok &= c[q] >= 0 && (uint32_t)c[q] < a.size[q];
         }
@@ -626,54 +639,69 @@ __global__ void grid_walk_kernel(GridWalkArgs a, uint32_t *err)
         }
         for (uint32_t j = 0; j < a.steps; ++j) {
             const U4 u = philox(i, a.t0 + j, a.k0, a.k1);
-            int32_t off[4] = {0, 0, 0, 0};
-            if (a.moore) {
-                // per dimension the admissible offsets (-1 if inside, 0, +1 if inside), in order
-                uint32_t v[4], lo[4], total = 1, center = 0, stride = 1;
-                for (uint32_t q = 0; q < a.d; ++q) {
-                    const bool dn = a.torus || c[q] > 0, up = a.torus || (uint32_t)c[q] + 1u < a.size[q];
+            int32_t off[D];
+#pragma unroll
+            for (uint32_t q = 0; q < D; ++q) off[q] = 0;
+            if constexpr (MOORE) {
+                // per dimension the admissible offsets (-1 if inside, 0, +1 if
+                // inside), in order; m enumerates their product, the all-zero
+                // offset left out
+                uint32_t v[D], lo[D], total = 1, center = 0;
+#pragma unroll
+                for (uint32_t q = 0; q < D; ++q) {
+                    const bool dn = TORUS || c[q] > 0, up = TORUS || (uint32_t)c[q] + 1u < a.size[q];
                     lo[q] = dn ? 1u : 0u;  // index of the zero offset in this dimension's list
                     v[q] = 1u + (dn ? 1u : 0u) + (up ? 1u : 0u);
-                    center += lo[q] * stride;
-                    stride *= v[q];
+                    center += lo[q] * total;
                     total *= v[q];
                 }
                 const uint32_t cnt = total - 1u;
                 if (cnt == 0) continue;
                 uint32_t m = below(u.w0, cnt);
                 if (m >= center) ++m;  // skip the zero offset
-                for (uint32_t q = 0; q < a.d; ++q) {
-                    off[q] = (int32_t)(m % v[q]) - (int32_t)lo[q];
-                    m /= v[q];
+#pragma unroll
+                for (uint32_t q = 0; q < D; ++q) {
+                    const uint32_t r = TORUS ? m % 3u : divmod123(m, v[q]);
+                    if (TORUS) m /= 3u;
+                    off[q] = (int32_t)r - (int32_t)lo[q];
                 }
             } else {
+                // von Neumann: the admissible unit moves, dimension by
+                // dimension, -1 before +1
                 uint32_t cnt = 0;
-                for (uint32_t q = 0; q < a.d; ++q) {
-                    cnt += (a.torus || c[q] > 0) ? 1u : 0u;
-                    cnt += (a.torus || (uint32_t)c[q] + 1u < a.size[q]) ? 1u : 0u;
+#pragma unroll
+                for (uint32_t q = 0; q < D; ++q) {
+                    cnt += (TORUS || c[q] > 0) ? 1u : 0u;
+                    cnt += (TORUS || (uint32_t)c[q] + 1u < a.size[q]) ? 1u : 0u;
                 }
                 if (cnt == 0) continue;
                 uint32_t m = below(u.w0, cnt);
-                for (uint32_t q = 0; q < a.d; ++q) {
-                    if (a.torus || c[q] > 0) {
+                bool done = false;
+#pragma unroll
+                for (uint32_t q = 0; q < D; ++q) {
+                    if (!done && (TORUS || c[q] > 0)) {
                         if (m == 0) {
                             off[q] = -1;
-                            break;
+                            done = true;
+                        } else {
+                            --m;
                         }
-                        --m;
                     }
-                    if (a.torus || (uint32_t)c[q] + 1u < a.size[q]) {
+                    if (!done && (TORUS || (uint32_t)c[q] + 1u < a.size[q])) {
                         if (m == 0) {
                             off[q] = 1;
-                            break;
+                            done = true;
+                        } else {
+                            --m;
                         }
-                        --m;
                     }
                 }
             }
-            for (uint32_t q = 0; q < a.d; ++q) c[q] = wrap_coord(c[q], off[q], a.size[q]);
+#pragma unroll
+            for (uint32_t q = 0; q < D; ++q) c[q] = wrap_coord(c[q], off[q], a.size[q]);
         }
-        for (uint32_t q = 0; q < a.d; ++q) a.c[q][i] = c[q];
+#pragma unroll
+        for (uint32_t q = 0; q < D; ++q) a.c[q][i] = c[q];
     }
 }
 
@@ -1367,7 +1395,21 @@ amb_status amb_table_grid_walk(amb_table *t, const int *cols, uint32_t d, const 
     a.steps = steps;
     a.moore = moore != 0;
     a.torus = torus != 0;
-    grid_walk_kernel<<<grid_for(t->n, 256, 152u * 32u), 256, 0, t->stream>>>(a, t->err);
+    const unsigned g = grid_for(t->n, 256, 152u * 32u);
+#define GW_CASE(D)                                                                                 \
+    case D:                                                                                        \
+        if (a.moore && a.torus) grid_walk_kernel<D, true, true><<<g, 256, 0, t->stream>>>(a, t->err);   \
+        if (a.moore && !a.torus) grid_walk_kernel<D, true, false><<<g, 256, 0, t->stream>>>(a, t->err); \
+        if (!a.moore && a.torus) grid_walk_kernel<D, false, true><<<g, 256, 0, t->stream>>>(a, t->err); \
+        if (!a.moore && !a.torus) grid_walk_kernel<D, false, false><<<g, 256, 0, t->stream>>>(a, t->err); \
+        break;
+    switch (d) {
+        GW_CASE(1)
+        GW_CASE(2)
+        GW_CASE(3)
+        GW_CASE(4)
+    }
+#undef GW_CASE
     AMB_TRY_CUDA(cudaGetLastError());
     return AMB_OK;
 }
