@@ -46,8 +46,12 @@ struct amb_log {
     uint32_t capacity = 0, count = 0;
     int32_t *ids = nullptr, *cols = nullptr;
     int64_t *vals = nullptr;
-    std::vector<int32_t *> win;  // per column: the winning record per row (-1 = none), when used
+    // per column: the number of the winning record per row (-1 = none), when
+    // used.  Records are numbered across flushes (base + index), so words
+    // left by earlier flushes never match and need no reset.
+    std::vector<int32_t *> win;
     std::vector<bool> used;      // columns recorded since the last flush
+    uint32_t base = 0;           // number of the first record of the next flush
 };
 
 struct amb_view {
@@ -564,30 +568,23 @@ struct LogCols {
 };
 
 __global__ void log_claim_kernel(const int32_t *__restrict__ ids, const int32_t *__restrict__ cols, uint32_t k,
-                                 LogCols lc)
+                                 uint32_t base, LogCols lc)
 {
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < k; e += gridDim.x * blockDim.x)
-        atomicMax(&lc.win[cols[e]][ids[e]], (int32_t)e);
+        atomicMax(&lc.win[cols[e]][ids[e]], (int32_t)(base + e));
 }
 
 __global__ void log_apply_kernel(const int32_t *__restrict__ ids, const int32_t *__restrict__ cols,
-                                 const int64_t *__restrict__ vals, uint32_t k, LogCols lc)
+                                 const int64_t *__restrict__ vals, uint32_t k, uint32_t base, LogCols lc)
 {
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < k; e += gridDim.x * blockDim.x) {
         const int32_t c = cols[e], id = ids[e];
-        if (lc.win[c][id] != (int32_t)e) continue;  // a later record of this row wins
+        if (lc.win[c][id] != (int32_t)(base + e)) continue;  // a later record of this row wins
         if (lc.dtype[c] == AMB_DT_I32)
             static_cast<int32_t *>(lc.ptr[c])[id] = (int32_t)(uint32_t)(uint64_t)vals[e];
         else
             static_cast<uint8_t *>(lc.ptr[c])[id] = (uint8_t)(uint64_t)vals[e];
     }
-}
-
-__global__ void log_reset_kernel(const int32_t *__restrict__ ids, const int32_t *__restrict__ cols, uint32_t k,
-                                 LogCols lc)
-{
-    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < k; e += gridDim.x * blockDim.x)
-        lc.win[cols[e]][ids[e]] = -1;
 }
 
 __global__ void fill_i32_kernel(int32_t *__restrict__ p, uint32_t k, int32_t v)
@@ -1332,6 +1329,13 @@ amb_status amb_log_flush(amb_log *l)
     cudaStream_t s = t->stream;
     if (l->count == 0) return AMB_OK;
     if (l->win.size() < t->cols.size()) l->win.resize(t->cols.size(), nullptr);
+    // record numbers stay below 2^31: start again from 0 with cleared words
+    // when this flush would pass that
+    if ((uint64_t)l->base + l->count >= 0x7FFFFFFFull) {
+        for (int32_t *w : l->win)
+            if (w) AMB_TRY_CUDA(cudaMemsetAsync(w, 0xFF, (size_t)t->n * sizeof(int32_t), s));
+        l->base = 0;
+    }
     LogCols lc;
     memset(&lc, 0, sizeof(lc));
     for (size_t c = 0; c < t->cols.size() && c < (size_t)kMaxLogCols; ++c) {
@@ -1344,10 +1348,10 @@ amb_status amb_log_flush(amb_log *l)
         lc.win[c] = l->win[c];
     }
     const unsigned g = grid_for(l->count, 256, 152u * 16u);
-    log_claim_kernel<<<g, 256, 0, s>>>(l->ids, l->cols, l->count, lc);
-    log_apply_kernel<<<g, 256, 0, s>>>(l->ids, l->cols, l->vals, l->count, lc);
-    log_reset_kernel<<<g, 256, 0, s>>>(l->ids, l->cols, l->count, lc);
+    log_claim_kernel<<<g, 256, 0, s>>>(l->ids, l->cols, l->count, l->base, lc);
+    log_apply_kernel<<<g, 256, 0, s>>>(l->ids, l->cols, l->vals, l->count, l->base, lc);
     AMB_TRY_CUDA(cudaGetLastError());
+    l->base += l->count;
     l->count = 0;
     std::fill(l->used.begin(), l->used.end(), false);
     return AMB_OK;
