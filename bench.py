@@ -69,6 +69,9 @@ def profiled_traffic(key):
     return profiled(key)
 
 
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -664,7 +667,9 @@ def gpu_arm(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "peak_kind": peak_kind, "traffic": traffic, "bytes_per_agent_step": b_alg,
                      "layout_bytes_per_agent_step": b_layout, "layout_frac": b_layout * n / (step_ms / 1e3) / 1e9 / hbm,
-                     "kernel_ms_median": step_ms, "issue": issue},
+                     "kernel_ms_median": step_ms, "issue": issue,
+                     # the same against the nominal HBM3e bandwidth (context only)
+                     "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "nominal_gbs": NOMINAL_HBM_GBS},
         "cpu_baseline": None if only_sir else cpu_baseline(),
         "e2e": None if only_sir else {"value": e2e_val, "unit": "agent-steps/s",
                                       "h2d_bytes_per_step": e2e["h2d_bytes_per_step"],
