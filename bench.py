@@ -449,6 +449,10 @@ def views_bench(amb, torch, stream, hbm, n=100_000_000, reps=5):
     out["where"] = {"ms": ms, "bytes": 4 * n + 4 * k, "selected": k}
     ms = timed(lambda: v.map("c", "mul", 1))
     out["view_map_filtered"] = {"ms": ms, "bytes": 12 * k}
+    # a view of that view (conjunction): the list read, the column gathered
+    # through it, the selected ids written
+    ms = timed(lambda: v.where("c", "==", 1).close())
+    out["where_of_view"] = {"ms": ms, "bytes": 8 * k + 4 * k, "selected": k}
     ids = torch.from_numpy(rng.integers(0, n, n // 10, dtype=np.int32)).cuda()
     torch.cuda.synchronize()
     sv = t.at(ids)

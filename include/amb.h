@@ -489,7 +489,8 @@ amb_status amb_view_from_ids(amb_table *t, const int32_t *ids, size_t k, int ids
 /* Scatter view of random ids, one per id i of v, in v's order: u = Philox
  * (key (seed, replicate), counter (i, step, 0, 0)), r' = hi32(u[word] * m);
  * exclude_self: m = range - 1 and r = r' + (r' >= i) (a uniformly chosen other
- * id, range >= 2); otherwise m = range and r = r' (range >= 1). */
+ * id, range >= 2); otherwise m = range and r = r' (range >= 1).  The drawn ids
+ * address rows of the table: range <= n, else AMB_EINVAL. */
 amb_status amb_view_draw(amb_view *v, uint64_t seed, uint32_t replicate, uint32_t step, uint32_t word, uint32_t range,
                          int exclude_self, amb_view **out);
 /* A view of a view: the ids v lists (in v's order, repeats kept) whose value

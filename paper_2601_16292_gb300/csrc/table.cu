@@ -39,6 +39,7 @@ struct amb_table {
     uint32_t *where_bits = nullptr;
     int32_t *where_cnt = nullptr, *where_off = nullptr;
     uint32_t *where_done = nullptr;  // blocks of the flag launch that finished (the last resets it)
+    uint32_t where_tiles = 0;        // write tiles the scratch holds
 };
 
 struct amb_log {
@@ -158,32 +159,46 @@ __global__ void __launch_bounds__(kMapNT) map_col_kernel(D *__restrict__ d, cons
 
 // ---------------------------------------------------------------- where ---
 // Order-preserving compaction in two streaming launches with no chain between
-// tiles.  (1) Every block reads a span of the column, 8 consecutive rows per
-// thread and span row (2 x 16 bytes of int32, 8 bytes of uint8), writes their
-// predicate bits as one byte to shared memory, so that the block's shared
-// bytes are the span's bitmap in row order, stores the bitmap and the count
-// of every write tile (kWhereTile rows); the last block to finish scans the
-// counts.  (2) One block per write tile turns its bitmap into ids, each warp
-// writing the selected rows of each 32-row word as one contiguous run.
+// tiles, over the rows of a column or, for a view of a view, over the entries
+// of a view's id list (the column read through the ids; list order kept).
+// (1) Every block reads a span, 8 consecutive positions per thread and span
+// row (2 x 16 bytes of int32 values or ids, 8 bytes of uint8 values), writes
+// their predicate bits as one byte to shared memory, so that the block's
+// shared bytes are the span's bitmap in position order, stores the bitmap and
+// the count of every write tile (kWhereTile positions); the last block to
+// finish scans the counts.  (2) One block per write tile turns its bitmap
+// into ids, each warp writing the selected positions of each 32-position word
+// as one contiguous run.
 constexpr int kWhereNT = 512;
-constexpr uint32_t kWhereTile = 32u * kWhereNT;        // rows per write tile: one predicate word per thread
+constexpr uint32_t kWhereTile = 32u * kWhereNT;        // positions per write tile: one predicate word per thread
 constexpr uint32_t kWhereWords = kWhereTile / 32u;
-constexpr int kWhereRowsI32 = 8;   // span rows of an int32 column
-constexpr int kWhereRowsU8 = 16;   // span rows of a uint8 column
-template <class T>
+constexpr int kWhereRowsI32 = 8;   // span rows over int32 values or over a list
+constexpr int kWhereRowsU8 = 16;   // span rows over uint8 values
+template <class T, bool kList>
 struct WhereSpan {
-    static constexpr uint32_t kRows = sizeof(T) == 4 ? kWhereRowsI32 : kWhereRowsU8;  // 8 column rows per thread each
+    static constexpr uint32_t kRows = (kList || sizeof(T) == 4) ? kWhereRowsI32 : kWhereRowsU8;  // 8 positions per thread each
     static constexpr uint32_t kBytes = kRows * kWhereNT;          // bitmap bytes of a span
-    static constexpr uint32_t kItems = kBytes * 8u;               // column rows of a span
+    static constexpr uint32_t kItems = kBytes * 8u;               // positions of a span
     static constexpr uint32_t kTiles = kItems / kWhereTile;       // write tiles per span
 };
 
-template <int CMP, class T>
-__device__ __forceinline__ uint32_t where_bits8(const T *__restrict__ c, uint32_t i, uint32_t n, int64_t s)
+// predicate bits of positions i .. i + 7 (bit k: position i + k); the value at
+// position p is c[p], or c[in[p]] over a list
+template <int CMP, class T, bool kList>
+__device__ __forceinline__ uint32_t where_bits8(const T *__restrict__ c, const int32_t *__restrict__ in, uint32_t i,
+                                                uint32_t n, int64_t s)
 {
     uint32_t f = 0;
     if (i + 8u <= n) {
-        if constexpr (sizeof(T) == 4) {
+        if constexpr (kList) {
+            const int4 a = *reinterpret_cast<const int4 *>(in + i), b = *reinterpret_cast<const int4 *>(in + i + 4);
+            const int32_t id[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+            T v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = c[id[k]];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) f |= (uint32_t)compare<CMP>((int64_t)v[k], s) << k;
+        } else if constexpr (sizeof(T) == 4) {
             const int4 a = *reinterpret_cast<const int4 *>(c + i), b = *reinterpret_cast<const int4 *>(c + i + 4);
             const int32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 #pragma unroll
@@ -196,28 +211,32 @@ __device__ __forceinline__ uint32_t where_bits8(const T *__restrict__ c, uint32_
         }
     } else {
         for (uint32_t k = 0; k < 8u; ++k)
-            if (i + k < n && compare<CMP>((int64_t)c[i + k], s)) f |= 1u << k;
+            if (i + k < n && compare<CMP>((int64_t)c[kList ? (uint32_t)in[i + k] : i + k], s)) f |= 1u << k;
     }
     return f;
 }
 
-template <int CMP, class T>
-__global__ void __launch_bounds__(kWhereNT) where_flags_kernel(const T *__restrict__ c, uint32_t n, int64_t s,
-                                                               uint32_t *__restrict__ bits, int32_t *__restrict__ cnt,
-                                                               int32_t *__restrict__ off, uint32_t n_tiles,
-                                                               uint32_t *__restrict__ done,
+// n positions, or *n_dev of them when n_dev is given (a view's length)
+template <int CMP, class T, bool kList>
+__global__ void __launch_bounds__(kWhereNT) where_flags_kernel(const T *__restrict__ c, const int32_t *__restrict__ in,
+                                                               uint32_t n, const uint32_t *__restrict__ n_dev,
+                                                               int64_t s, uint32_t *__restrict__ bits,
+                                                               int32_t *__restrict__ cnt, int32_t *__restrict__ off,
+                                                               uint32_t n_tiles, uint32_t *__restrict__ done,
                                                                uint32_t *__restrict__ count)
 {
-    using Sp = WhereSpan<T>;
+    using Sp = WhereSpan<T, kList>;
     __shared__ __align__(16) uint8_t s_map[Sp::kBytes];
     __shared__ uint32_t s_sum[Sp::kTiles][kWhereNT / 32];
     __shared__ uint32_t s_warp[kWhereNT / 32 + 1];
     __shared__ bool s_last;
     const uint32_t tid = threadIdx.x, lane = tid & 31u, wid = tid >> 5;
+    const uint32_t len = n_dev ? *n_dev : n;
     const uint32_t span0 = blockIdx.x * Sp::kItems;
 #pragma unroll 4
     for (uint32_t r = 0; r < Sp::kRows; ++r)
-        s_map[r * kWhereNT + tid] = (uint8_t)where_bits8<CMP>(c, span0 + (r * kWhereNT + tid) * 8u, n, s);
+        s_map[r * kWhereNT + tid] =
+            (uint8_t)where_bits8<CMP, T, kList>(c, in, span0 + (r * kWhereNT + tid) * 8u, len, s);
     __syncthreads();
     // word tid + k kWhereNT of the span is word tid of its write tile k
     const uint32_t *wmap = reinterpret_cast<const uint32_t *>(s_map);
@@ -278,25 +297,29 @@ __global__ void __launch_bounds__(kWhereNT) where_flags_kernel(const T *__restri
     }
 }
 
-// Ids of a write tile's selected rows from slot `first` on.  Thread t holds
-// word t (rows tile0 + 32 t ..) and its exclusive count `ex` within the tile;
-// the warp writes each of its 32 words' rows as one contiguous run.
+// Ids of a write tile's selected positions from slot `first` on.  Thread t
+// holds word t (positions tile0 + 32 t ..) and its exclusive count `ex` within
+// the tile; the warp writes each of its 32 words' ids as one contiguous run
+// (the position itself, or the list entry there).
+template <bool kList>
 __device__ __forceinline__ void where_emit(uint32_t word, uint32_t ex, uint32_t first, uint32_t tile0,
-                                           int32_t *__restrict__ ids)
+                                           const int32_t *__restrict__ in, int32_t *__restrict__ ids)
 {
     const uint32_t lane = threadIdx.x & 31u, lt = (1u << lane) - 1u;
-    const uint32_t slot = first + ex, row0 = tile0 + threadIdx.x * 32u;
+    const uint32_t slot = first + ex, pos0 = tile0 + threadIdx.x * 32u;
 #pragma unroll 4
     for (int j = 0; j < 32; ++j) {
         const uint32_t m = __shfl_sync(0xffffffffu, word, j);
         if (m == 0u) continue;  // warp-uniform
-        const uint32_t p = __shfl_sync(0xffffffffu, slot, j), r0 = __shfl_sync(0xffffffffu, row0, j);
-        if ((m >> lane) & 1u) ids[p + __popc(m & lt)] = (int32_t)(r0 + lane);
+        const uint32_t p = __shfl_sync(0xffffffffu, slot, j), q0 = __shfl_sync(0xffffffffu, pos0, j);
+        if ((m >> lane) & 1u) ids[p + __popc(m & lt)] = kList ? in[q0 + lane] : (int32_t)(q0 + lane);
     }
 }
 
+template <bool kList>
 __global__ void __launch_bounds__(kWhereNT) where_write_kernel(const uint32_t *__restrict__ bits,
                                                                const int32_t *__restrict__ off,
+                                                               const int32_t *__restrict__ in,
                                                                int32_t *__restrict__ ids)
 {
     __shared__ uint32_t s_warp[kWhereNT / 32 + 1];
@@ -304,75 +327,28 @@ __global__ void __launch_bounds__(kWhereNT) where_write_kernel(const uint32_t *_
     const uint32_t word = bits[(size_t)tile * kWhereWords + threadIdx.x];
     uint32_t total;
     const uint32_t ex = block_exclusive_scan<kWhereNT>(__popc(word), s_warp, &total);
-    where_emit(word, ex, (uint32_t)off[tile], tile * kWhereTile, ids);
+    where_emit<kList>(word, ex, (uint32_t)off[tile], tile * kWhereTile, in, ids);
 }
 
-// A table of one write tile: both steps in one block.
-template <int CMP, class T>
-__global__ void __launch_bounds__(kWhereNT) where_single_kernel(const T *__restrict__ c, uint32_t n, int64_t s,
+// At most one write tile of positions: both steps in one block.
+template <int CMP, class T, bool kList>
+__global__ void __launch_bounds__(kWhereNT) where_single_kernel(const T *__restrict__ c,
+                                                                const int32_t *__restrict__ in, uint32_t n,
+                                                                const uint32_t *__restrict__ n_dev, int64_t s,
                                                                 int32_t *__restrict__ ids, uint32_t *__restrict__ count)
 {
     __shared__ __align__(16) uint8_t s_map[kWhereWords * 4u];
     __shared__ uint32_t s_warp[kWhereNT / 32 + 1];
     const uint32_t tid = threadIdx.x;
-    for (uint32_t b = tid; b < kWhereWords * 4u; b += kWhereNT) s_map[b] = (uint8_t)where_bits8<CMP>(c, b * 8u, n, s);
+    const uint32_t len = n_dev ? *n_dev : n;
+    for (uint32_t b = tid; b < kWhereWords * 4u; b += kWhereNT)
+        s_map[b] = (uint8_t)where_bits8<CMP, T, kList>(c, in, b * 8u, len, s);
     __syncthreads();
     const uint32_t word = reinterpret_cast<const uint32_t *>(s_map)[tid];
     uint32_t total;
     const uint32_t ex = block_exclusive_scan<kWhereNT>(__popc(word), s_warp, &total);
-    where_emit(word, ex, 0u, 0u, ids);
+    where_emit<kList>(word, ex, 0u, 0u, in, ids);
     if (tid == 0) *count = total;
-}
-
-// A view of a view: the listed ids (list order) whose value satisfies the
-// predicate.  Same tiling as where_kernel; the column is read through the ids.
-constexpr int kVwNT = 256;
-constexpr int kVwItems = 16;
-constexpr uint32_t kVwTile = kVwNT * kVwItems;
-
-template <int CMP, class T>
-__global__ void __launch_bounds__(kVwNT) view_where_kernel(const T *__restrict__ c, const int32_t *__restrict__ in,
-                                                            const uint32_t *__restrict__ in_count, int64_t s,
-                                                            int32_t *__restrict__ ids, uint32_t *__restrict__ count,
-                                                            uint32_t n_tiles, unsigned long long *tickets,
-                                                            uint32_t parity, uint64_t *status, uint32_t epoch,
-                                                            uint32_t *err)
-{
-    __shared__ uint32_t s_tile, s_prefix;
-    __shared__ uint32_t s_warp[kVwNT / 32 + 1];
-    __shared__ int32_t s_ids[kVwTile];
-    const uint32_t tid = threadIdx.x, k = *in_count;
-    if (blockIdx.x == 0 && tid == 0) tickets[parity ^ 1u] = 0ull;
-    for (;;) {
-        if (tid == 0) s_tile = (uint32_t)atomicAdd(&tickets[parity], 1ull);
-        __syncthreads();
-        const uint32_t tile = s_tile;
-        __syncthreads();
-        if (tile >= n_tiles) break;
-        const uint32_t i0 = tile * kVwTile + tid * kVwItems;
-        uint32_t bits = 0;
-        int32_t id[kVwItems];
-#pragma unroll
-        for (int q = 0; q < kVwItems; ++q) {
-            id[q] = (i0 + q < k) ? in[i0 + q] : -1;
-            if (id[q] >= 0 && compare<CMP>((int64_t)c[id[q]], s)) bits |= 1u << q;
-        }
-        uint32_t total;
-        const uint32_t ex = block_exclusive_scan<kVwNT>(__popc(bits), s_warp, &total);
-        uint32_t pos = ex;
-#pragma unroll
-        for (int q = 0; q < kVwItems; ++q)
-            if (bits & (1u << q)) s_ids[pos++] = id[q];
-        if (tid < 32) {
-            const uint32_t pre = warp_lookback(status, tile, epoch, total, err);
-            if (tid == 0) s_prefix = pre;
-        }
-        __syncthreads();
-        const uint32_t pre = s_prefix;
-        for (uint32_t j = tid; j < total; j += kVwNT) ids[pre + j] = s_ids[j];
-        if (tile == n_tiles - 1u && tid == 0) *count = pre + total;
-        __syncthreads();
-    }
 }
 
 // scatter_add with one value per listed id
@@ -761,34 +737,53 @@ amb_status launch_map_col_t(D *d, const S *src, uint32_t n, int op, cudaStream_t
     return AMB_OK;
 }
 
-template <class T>
-amb_status launch_where_t(amb_table *t, const T *c, int cmp, int64_t s, amb_view *v)
+// Scratch of where(): predicate words, per-tile counts and their scan for up
+// to `tiles` write tiles (grown on demand: a view's list may be longer than
+// the table).  Frees are stream-ordered, after any launch still using them.
+amb_status ensure_where_scratch(amb_table *t, uint32_t tiles, cudaStream_t st)
 {
-    const uint32_t n = t->n;
-    cudaStream_t st = t->stream;
-    if (n == 0) {
-        AMB_TRY_CUDA(cudaMemsetAsync(v->count, 0, sizeof(uint32_t), st));
-        return AMB_OK;
-    }
-    const uint32_t n_tiles = (n + kWhereTile - 1u) / kWhereTile;
-    const uint32_t n_spans = (n + WhereSpan<T>::kItems - 1u) / WhereSpan<T>::kItems;
-    if (n_tiles > 1u && !t->where_bits) {
-        AMB_TRY(dalloc(&t->where_bits, (size_t)n_tiles * kWhereWords, st));
-        AMB_TRY(dalloc(&t->where_cnt, n_tiles, st));
-        AMB_TRY(dalloc(&t->where_off, (size_t)n_tiles + 1u, st));
+    if (!t->where_done) {
         AMB_TRY(dalloc(&t->where_done, 1, st));
         AMB_TRY_CUDA(cudaMemsetAsync(t->where_done, 0, sizeof(uint32_t), st));
     }
+    if (tiles <= t->where_tiles) return AMB_OK;
+    dfree(t->where_bits, st);
+    dfree(t->where_cnt, st);
+    dfree(t->where_off, st);
+    t->where_tiles = 0;
+    AMB_TRY(dalloc(&t->where_bits, (size_t)tiles * kWhereWords, st));
+    AMB_TRY(dalloc(&t->where_cnt, tiles, st));
+    AMB_TRY(dalloc(&t->where_off, (size_t)tiles + 1u, st));
+    t->where_tiles = tiles;
+    return AMB_OK;
+}
+
+// where over positions 0 .. n-1 of the column's rows (kList false) or of the
+// view list `in` (kList true; n_dev holds its length, at most n); the
+// selected ids, in position order, go to `out`.
+template <class T, bool kList>
+amb_status launch_where_t(amb_table *t, const T *c, const int32_t *in, uint32_t n, const uint32_t *n_dev, int cmp,
+                          int64_t s, amb_view *out)
+{
+    cudaStream_t st = t->stream;
+    if (n == 0) {
+        AMB_TRY_CUDA(cudaMemsetAsync(out->count, 0, sizeof(uint32_t), st));
+        return AMB_OK;
+    }
+    using Sp = WhereSpan<T, kList>;
+    const uint32_t n_tiles = (uint32_t)(((uint64_t)n + kWhereTile - 1u) / kWhereTile);
+    const uint32_t n_spans = (uint32_t)(((uint64_t)n + Sp::kItems - 1u) / Sp::kItems);
+    if (n_tiles > 1u) AMB_TRY(ensure_where_scratch(t, n_tiles, st));
 #define WHERE_CASE(C)                                                                                            \
     case C:                                                                                                      \
         if (n_tiles == 1u) {                                                                                     \
-            where_single_kernel<C, T><<<1, kWhereNT, 0, st>>>(c, n, s, v->ids, v->count);                        \
+            where_single_kernel<C, T, kList><<<1, kWhereNT, 0, st>>>(c, in, n, n_dev, s, out->ids, out->count);  \
         } else {                                                                                                 \
-            where_flags_kernel<C, T><<<n_spans, kWhereNT, 0, st>>>(c, n, s, t->where_bits, t->where_cnt,         \
-                                                                   t->where_off, n_tiles, t->where_done,        \
-                                                                   v->count);                                    \
+            where_flags_kernel<C, T, kList><<<n_spans, kWhereNT, 0, st>>>(c, in, n, n_dev, s, t->where_bits,     \
+                                                                          t->where_cnt, t->where_off, n_tiles,  \
+                                                                          t->where_done, out->count);           \
             AMB_TRY_CUDA(cudaGetLastError());                                                                    \
-            where_write_kernel<<<n_tiles, kWhereNT, 0, st>>>(t->where_bits, t->where_off, v->ids);              \
+            where_write_kernel<kList><<<n_tiles, kWhereNT, 0, st>>>(t->where_bits, t->where_off, in, out->ids); \
         }                                                                                                        \
         break;
     switch (cmp) {
@@ -1056,8 +1051,10 @@ amb_status amb_table_where(amb_table *t, int col, amb_cmp cmp, int64_t scalar, a
     amb_view *v = nullptr;
     AMB_TRY(new_view(t, t->n, true, &v));
     const amb_status st = c->dtype == AMB_DT_I32
-                              ? launch_where_t(t, static_cast<const int32_t *>(c->ptr), cmp, scalar, v)
-                              : launch_where_t(t, static_cast<const uint8_t *>(c->ptr), cmp, scalar, v);
+                              ? launch_where_t<int32_t, false>(t, static_cast<const int32_t *>(c->ptr), nullptr, t->n,
+                                                               nullptr, cmp, scalar, v)
+                              : launch_where_t<uint8_t, false>(t, static_cast<const uint8_t *>(c->ptr), nullptr, t->n,
+                                                               nullptr, cmp, scalar, v);
     if (st != AMB_OK) {
         amb_view_destroy(v);
         return st;
@@ -1106,9 +1103,11 @@ amb_status amb_view_draw(amb_view *v, uint64_t seed, uint32_t replicate, uint32_
     *out = nullptr;
     if (seed > 0xFFFFFFFFull) return fail(AMB_EINVAL, "seed must be < 2^32");
     if (word > 3) return fail(AMB_EINVAL, "word must be 0..3");
-    if (range > 0x80000000u || range < (exclude_self ? 2u : 1u))
-        return fail(AMB_EINVAL, "range %u out of bounds (exclude_self needs >= 2)", range);
     amb_table *t = v->t;
+    // the drawn ids address rows of the table, so the range is at most n
+    if (range > t->n || range < (exclude_self ? 2u : 1u))
+        return fail(AMB_EINVAL, "range %u out of bounds (at most the table's %u rows; exclude_self needs >= 2)", range,
+                    t->n);
     amb_view *r = nullptr;
     AMB_TRY(new_view(t, v->capacity, false, &r));
     if (v->capacity) {
@@ -1136,46 +1135,12 @@ amb_status amb_view_where(amb_view *v, int col, amb_cmp cmp, int64_t scalar, amb
     if ((int)cmp < 0 || (int)cmp > AMB_CMP_GE) return fail(AMB_EINVAL, "unknown comparison %d", (int)cmp);
     amb_view *r = nullptr;
     AMB_TRY(new_view(t, v->capacity, v->unique, &r));
-    cudaStream_t st = t->stream;
-    amb_status res = AMB_OK;
-    if (v->capacity == 0) {
-        if (cudaMemsetAsync(r->count, 0, sizeof(uint32_t), st) != cudaSuccess) res = fail(AMB_ECUDA, "memset failed");
-    } else {
-        const uint32_t n_tiles = (v->capacity + kVwTile - 1u) / kVwTile;
-        res = t->lb.ensure(n_tiles, st);
-        if (res == AMB_OK) {
-            uint32_t parity, epoch;
-            t->lb.next(&parity, &epoch);
-            const unsigned g = std::min<uint32_t>(n_tiles, 152u * 8u);
-#define VW_CASE(C, T)                                                                                               \
-    case C:                                                                                                         \
-        view_where_kernel<C, T><<<g, kVwNT, 0, st>>>(static_cast<const T *>(c->ptr), v->ids, v->count, scalar, r->ids, \
-                                                     r->count, n_tiles, t->lb.tickets, parity, t->lb.status, epoch,  \
-                                                     t->err);                                                        \
-        break;
-            if (c->dtype == AMB_DT_I32) {
-                switch (cmp) {
-                    VW_CASE(AMB_CMP_EQ, int32_t)
-                    VW_CASE(AMB_CMP_NE, int32_t)
-                    VW_CASE(AMB_CMP_LT, int32_t)
-                    VW_CASE(AMB_CMP_LE, int32_t)
-                    VW_CASE(AMB_CMP_GT, int32_t)
-                    VW_CASE(AMB_CMP_GE, int32_t)
-                }
-            } else {
-                switch (cmp) {
-                    VW_CASE(AMB_CMP_EQ, uint8_t)
-                    VW_CASE(AMB_CMP_NE, uint8_t)
-                    VW_CASE(AMB_CMP_LT, uint8_t)
-                    VW_CASE(AMB_CMP_LE, uint8_t)
-                    VW_CASE(AMB_CMP_GT, uint8_t)
-                    VW_CASE(AMB_CMP_GE, uint8_t)
-                }
-            }
-#undef VW_CASE
-            if (cudaGetLastError() != cudaSuccess) res = fail(AMB_ECUDA, "view_where launch failed");
-        }
-    }
+    const amb_status res =
+        c->dtype == AMB_DT_I32
+            ? launch_where_t<int32_t, true>(t, static_cast<const int32_t *>(c->ptr), v->ids, v->capacity, v->count,
+                                            cmp, scalar, r)
+            : launch_where_t<uint8_t, true>(t, static_cast<const uint8_t *>(c->ptr), v->ids, v->capacity, v->count,
+                                            cmp, scalar, r);
     if (res != AMB_OK) {
         amb_view_destroy(r);
         return res;

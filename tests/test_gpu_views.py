@@ -182,6 +182,12 @@ def test_errors(stream):
     with pytest.raises(amb.AmbError) as e:
         v.draw(1, 0, 0, 0, 1, True)
     assert e.value.status == amb.AMB_EINVAL
+    # drawn ids address rows: the range is at most the table's n
+    with pytest.raises(amb.AmbError) as e:
+        v.draw(1, 0, 0, 0, 11, False)
+    assert e.value.status == amb.AMB_EINVAL
+    with v.draw(1, 0, 0, 0, 10, True) as r:
+        assert r.count() == 10 and int(r.ids().max()) < 10
     with pytest.raises(amb.AmbError) as e:
         amb.lib()  # the table refuses to go while a view is alive
         amb._check(amb.lib().amb_table_destroy(t.handle))
@@ -193,8 +199,10 @@ def test_errors(stream):
     empty.add_column("c", "i32")
     with empty.where("c", "==", 0) as v:
         assert v.count() == 0
-        with v.draw(1, 0, 0, 0, 5, True) as r:
-            assert r.count() == 0
+        with v.where("c", ">", 0) as w:
+            assert w.count() == 0
+        with pytest.raises(amb.AmbError):  # no row to draw
+            v.draw(1, 0, 0, 0, 1, False)
     empty.map("c", "add", 1)
     assert empty.read("c").numel() == 0
     empty.close()
