@@ -12,8 +12,8 @@
  * (snapshot-then-apply) semantics throughout (paper Sec. 3.4): every agent
  * reads the state as it was at the start of the step.
  *
- * Readings of the paper where it is silent are listed in the design doc; the ones
- * this file implements are restated next to the code that implements them.
+ * Where the paper is silent, the reading taken is stated next to the code
+ * that implements it.
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -shared -fPIC (oracle/build.py).
  * -ffp-contract=off matters: the threshold tables are defined by individual
