@@ -20,7 +20,7 @@ def _wrapped_delta(a, b, L):
     return d
 
 
-def test_in_bounds_cfg2_prefix():
+def test_in_bounds_walk_1000_torus_prefix():
     p = oracle.Population("walk", 200_000, seed=1, L=1000)
     assert p.x.min() >= 0 and p.x.max() < 1000 and p.y.min() >= 0 and p.y.max() < 1000
     p.step(20)

@@ -19,7 +19,7 @@ from scipy import stats
 import oracle
 
 
-def test_conservation_and_donors_cfg1():
+def test_conservation_and_donors_10k_agents():
     n = 10_000
     p = oracle.Population("wealth", n, seed=0)
     assert np.all(p.w == 1)
