@@ -86,6 +86,19 @@ def test_where_large_sparse_and_dense(stream):
     t.close()
 
 
+def test_where_more_tiles_than_the_fast_count_scan(stream):
+    # > 8,192 write tiles of 16,384 rows: the count scan of the last block
+    # takes its loop form (more than 16 tiles per thread)
+    n = (1 << 27) + (1 << 22) + 5
+    col = RNG.integers(0, 3, n).astype(np.uint8)
+    t = _table(n, stream, {"c": col})
+    with t.where("c", "==", 1) as v:
+        ids = v.ids()
+        want = np.flatnonzero(col == 1)
+        assert ids.size == want.size and np.array_equal(ids, want)
+    t.close()
+
+
 @pytest.mark.parametrize("dtype", [np.int32, np.uint8])
 @pytest.mark.parametrize("op,s", [("add", 3), ("sub", 5), ("mul", 3), ("min", 10), ("max", 200), ("set", 9)])
 def test_updates_through_views(stream, dtype, op, s):
