@@ -305,14 +305,18 @@ template <bool kList>
 __device__ __forceinline__ void where_emit(uint32_t word, uint32_t ex, uint32_t first, uint32_t tile0,
                                            const int32_t *__restrict__ in, int32_t *__restrict__ ids)
 {
-    const uint32_t lane = threadIdx.x & 31u, lt = (1u << lane) - 1u;
-    const uint32_t slot = first + ex, pos0 = tile0 + threadIdx.x * 32u;
-#pragma unroll 4
+    const uint32_t lane = threadIdx.x & 31u, bit = 1u << lane, lt = bit - 1u;
+    const uint32_t slot = first + ex;
+    // word j of this warp covers positions pos + 32 j for this lane
+    const uint32_t pos = tile0 + (threadIdx.x & ~31u) * 32u + lane;
+#pragma unroll
     for (int j = 0; j < 32; ++j) {
         const uint32_t m = __shfl_sync(0xffffffffu, word, j);
-        if (m == 0u) continue;  // warp-uniform
-        const uint32_t p = __shfl_sync(0xffffffffu, slot, j), q0 = __shfl_sync(0xffffffffu, pos0, j);
-        if ((m >> lane) & 1u) ids[p + __popc(m & lt)] = kList ? in[q0 + lane] : (int32_t)(q0 + lane);
+        const uint32_t p = __shfl_sync(0xffffffffu, slot, j);
+        if (m & bit) {
+            const uint32_t q = pos + 32u * (uint32_t)j;
+            ids[p + __popc(m & lt)] = kList ? in[q] : (int32_t)q;
+        }
     }
 }
 
