@@ -32,7 +32,6 @@ struct amb_table {
     cudaStream_t stream = nullptr;
     std::vector<Column> cols;
     uint32_t *err = nullptr;
-    Lookback lb;
     int live_views = 0;
     // where() scratch, made on first use: predicate words, per-tile counts
     // and their exclusive scan
@@ -927,7 +926,6 @@ amb_status amb_table_destroy(amb_table *t)
     dfree(t->where_cnt, t->stream);
     dfree(t->where_off, t->stream);
     dfree(t->where_done, t->stream);
-    t->lb.release(t->stream);
     cudaStreamSynchronize(t->stream);
     delete t;
     return AMB_OK;
