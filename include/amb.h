@@ -581,6 +581,13 @@ amb_status amb_selfcheck_wait_timeout(void *cuda_stream, double *waited_s);
  * k = 0 turns it off.  Process-wide. */
 amb_status amb_debug_fail_creates(uint32_t k);
 
+/* Test hook (no counterpart in the paper): the number the log gives its next
+ * record.  A flush numbers its records from this value on and restarts from 0,
+ * with the winner words cleared, when the numbers would reach 2^31 - 1; the
+ * hook lets a test reach that restart without 2^31 records.  Fails with
+ * AMB_EINVAL while records are pending or for base >= 2^31. */
+amb_status amb_debug_log_base(amb_log *l, uint32_t base);
+
 /* Version string of the library build. */
 const char *amb_version(void);
 

@@ -174,6 +174,7 @@ def lib():
             "amb_log_pending": (st, [vp, ctypes.POINTER(sz)]),
             "amb_log_flush": (st, [vp]),
             "amb_log_destroy": (st, [vp]),
+            "amb_debug_log_base": (st, [vp, u32]),
             "amb_table_grid_walk": (st, [vp, ctypes.POINTER(ctypes.c_int), u32, ctypes.POINTER(u32), ctypes.c_int,
                                          ctypes.c_int, u64, u32, u32, u32]),
         }
@@ -852,6 +853,10 @@ class Log:
 
     def flush(self):
         _check(lib().amb_log_flush(self.handle))
+
+    def debug_base(self, base):
+        """Test hook: the number of the next record (see amb_debug_log_base)."""
+        _check(lib().amb_debug_log_base(self.handle, int(base)))
 
     def close(self):
         if self.handle is not None and self.handle.value:

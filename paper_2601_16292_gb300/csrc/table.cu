@@ -1324,6 +1324,15 @@ amb_status amb_log_flush(amb_log *l)
     return AMB_OK;
 }
 
+amb_status amb_debug_log_base(amb_log *l, uint32_t base)
+{
+    if (!l) return fail(AMB_EINVAL, "null log");
+    if (l->count) return fail(AMB_EINVAL, "records are pending");
+    if (base >= 0x80000000u) return fail(AMB_EINVAL, "base must be < 2^31");
+    l->base = base;
+    return AMB_OK;
+}
+
 amb_status amb_log_destroy(amb_log *l)
 {
     if (!l) return AMB_OK;

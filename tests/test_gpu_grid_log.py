@@ -65,6 +65,40 @@ def test_log_last_write_wins(stream):
     t.close()
 
 
+def test_log_record_numbers_restart(stream):
+    # flushes numbered near 2^31 - 1: the log restarts its numbers from 0 with
+    # the winner words cleared, and a stale winner word never matches
+    n = 3000
+    t = amb.Table(n, stream)
+    t.add_column("a", "i32", fill=0)
+    want = np.zeros(n, dtype=np.int32)
+    log = t.log(10_000)
+    ids = RNG.integers(0, 200, 5000).astype(np.int32)
+    vals = RNG.integers(-100, 100, 5000).astype(np.int64)
+    log.debug_base((1 << 31) - 6000)  # this flush fits below 2^31 - 1
+    log.record("a", ids, vals)
+    log.flush()
+    oracle.log_flush(want, ids, vals)
+    assert np.array_equal(t.read("a").numpy(), want)
+    # the next one would pass it: restart
+    ids2 = RNG.integers(0, 200, 5000).astype(np.int32)
+    vals2 = RNG.integers(-100, 100, 5000).astype(np.int64)
+    log.record("a", ids2, vals2)
+    log.flush()
+    oracle.log_flush(want, ids2, vals2)
+    assert np.array_equal(t.read("a").numpy(), want)
+    # rows written before the restart and not after keep their values; a few
+    # records on fresh numbers
+    log.record("a", np.array([7, 7, 9], dtype=np.int32), np.array([1, 2, 3], dtype=np.int64))
+    log.flush()
+    want[7], want[9] = 2, 3
+    assert np.array_equal(t.read("a").numpy(), want)
+    with pytest.raises(amb.AmbError):
+        log.debug_base(1 << 31)
+    log.close()
+    t.close()
+
+
 CASES = [(1, False, True, [7]), (1, True, False, [2]), (2, True, True, [33, 17]), (2, False, False, [5, 9]),
          (2, True, False, [1, 40]), (3, True, True, [6, 5, 4]), (3, False, False, [3, 3, 3]),
          (3, True, False, [2, 2, 2]), (4, True, True, [3, 4, 5, 6]), (4, False, False, [2, 3, 1, 4]),
