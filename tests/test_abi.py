@@ -125,6 +125,11 @@ def test_job_bytes_rejects_what_create_rejects():
         amb.amb_job_bytes(amb.make_job("sir", 10, seed=1, steps=1, L=4, beta=0.5, gamma=0.1, n0=11))
     with pytest.raises(amb.AmbError):
         amb.amb_job_bytes(amb.make_job("walk", 10, seed=1 << 33, steps=1, L=4))
+    # continuous-space models are not batched or served
+    for model in ("cwalk", "csir"):
+        with pytest.raises(amb.AmbError) as e:
+            amb.amb_job_bytes(amb.make_job(model, 10, seed=1, steps=1))
+        assert e.value.status == amb.AMB_EINVAL
 
 
 def test_injected_creation_failures_on_the_host():
