@@ -412,7 +412,7 @@ __device__ __forceinline__ void cas_update(uint32_t *word, F f, uint32_t *err)
 // loads, are independent requests in flight together.  Ids of a filtered view
 // are distinct, so all of a pass's reads can precede its writes; views that
 // may repeat ids update through atomics.
-constexpr int kViewU = 8;
+constexpr int kViewU = 16;
 constexpr uint32_t kNoId = 0xFFFFFFFFu;
 
 __device__ __forceinline__ void load_ids(const int32_t *__restrict__ ids, uint32_t i0, uint32_t k, uint32_t id[kViewU])

@@ -129,7 +129,8 @@ def test_updates_through_views(stream, dtype, op, s):
 @pytest.mark.parametrize("dtype", [np.int32, np.uint8])
 @pytest.mark.parametrize("op,s", [("add", 3), ("mul", 3), ("set", 9), ("max", 200)])
 def test_updates_through_views_large(stream, dtype, op, s):
-    # lists longer than one pass of the update kernels (8 ids per thread)
+    # a scatter list longer than one pass of the update kernels (a grid of
+    # 152 x 16 blocks of 256 threads, 16 ids per thread: 9,961,472 ids)
     n = (1 << 20) + 5
     col = _rand(dtype, n)
     t = _table(n, stream, {"c": col})
@@ -138,7 +139,7 @@ def test_updates_through_views_large(stream, dtype, op, s):
         f_ids = v.ids()
         v.map("c", op, s)
     oracle.view_map(want, f_ids, op, s)
-    ids = RNG.integers(0, n, 3 * n + 1).astype(np.int32)
+    ids = RNG.integers(0, n, 12_000_001).astype(np.int32)
     with t.at(ids) as v:
         v.map("c", op, s)
     oracle.view_map(want, ids, op, s)
