@@ -561,8 +561,15 @@ amb_status amb_table_grid_walk(amb_table *t, const int *cols, uint32_t d, const 
  *  - All calls share the one array and it keeps the last call's contents;
  *    the call clears what has to start at zero.  Calls that overlap on the
  *    GPU (other streams, other threads) race on it: serialise them.
+ *  - Each call starts by clearing, in stream order, the look-back words,
+ *    ticket counters and error word in that array, so no call depends on
+ *    what an earlier one left there.
  *  - sync != 0 waits for the result and reports coordinates outside [0, L)
- *    as AMB_EINVAL, as amb_cell_index does.
+ *    as AMB_EINVAL, as amb_cell_index does, and a look-back wait that ran out
+ *    as AMB_ETIMEOUT.  sync == 0 returns once the work is queued and reports
+ *    no device-side error at all (the next call clears the error word): such
+ *    a caller learns of left-out agents by checking start[L*L] == n after
+ *    synchronising the stream.
  */
 amb_status amb_cell_index_noalloc(const int32_t *x, const int32_t *y, uint32_t n, uint32_t L, int32_t *start,
                                   int32_t *ids, void *cuda_stream, int sync);

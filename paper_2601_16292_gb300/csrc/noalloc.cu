@@ -20,13 +20,15 @@ constexpr size_t kOffTickets = kOffStatus + (((size_t)kStaticTiles * 8u + 255u) 
 constexpr size_t kOffErr = kOffTickets + 256u;
 constexpr size_t kStaticBytes = kOffErr + 256u;  // about 8 MiB
 
-// Zero-initialised: the look-back words start as "not ready" and both ticket
-// counters at zero, which is what the first call needs.
+// Every call first clears, in stream order, the look-back words, both ticket
+// counters and the error word (one contiguous stretch of 2,308 bytes), so a
+// call never depends on what an earlier call, or any host-side count of
+// calls, left behind: each call runs its scan with the same ticket parity and
+// epoch.
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
 struct StaticSlot {
     unsigned char *base = nullptr;  // device address of g_static_scratch on this device
-    uint32_t launches = 0;          // calls so far: parity and epoch of the look-back
 };
 
 static std::mutex g_static_mu;
@@ -50,7 +52,6 @@ extern "C" amb_status amb_cell_index_noalloc(const int32_t *x, const int32_t *y,
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return fail(AMB_ECUDA, "no usable current device");
     unsigned char *base;
-    uint32_t parity, epoch;
     {
         // once per device, with that device current: the device address of
         // the array (host code cannot use the symbol itself)
@@ -64,9 +65,6 @@ extern "C" amb_status amb_cell_index_noalloc(const int32_t *x, const int32_t *y,
             slot.base = static_cast<unsigned char *>(p);
         }
         base = slot.base;
-        parity = slot.launches & 1u;
-        epoch = (slot.launches % 0x3FFFFFFFu) + 1u;
-        ++slot.launches;
     }
     cudaStream_t s = (cudaStream_t)cuda_stream;
     int32_t *cnt = reinterpret_cast<int32_t *>(base + kOffCnt);
@@ -74,8 +72,9 @@ extern "C" amb_status amb_cell_index_noalloc(const int32_t *x, const int32_t *y,
     uint64_t *status = reinterpret_cast<uint64_t *>(base + kOffStatus);
     unsigned long long *tickets = reinterpret_cast<unsigned long long *>(base + kOffTickets);
     uint32_t *err = reinterpret_cast<uint32_t *>(base + kOffErr);
-    AMB_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));  // the last call's error word
-    AMB_TRY(launch_cell_index_raw(x, y, n, L, start, ids, cnt, cursor, status, tickets, parity, epoch, err, s));
+    // look-back words ("not ready"), tickets and error word of the last call
+    AMB_TRY_CUDA(cudaMemsetAsync(base + kOffStatus, 0, kOffErr + sizeof(uint32_t) - kOffStatus, s));
+    AMB_TRY(launch_cell_index_raw(x, y, n, L, start, ids, cnt, cursor, status, tickets, 0u, 1u, err, s));
     if (!sync) return AMB_OK;
     uint32_t h = 0;
     AMB_TRY_CUDA(cudaMemcpyAsync(&h, err, sizeof(h), cudaMemcpyDeviceToHost, s));

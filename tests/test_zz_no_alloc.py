@@ -61,3 +61,66 @@ def test_noalloc_index_rejects_grids_beyond_its_scratch():
     with pytest.raises(amb.AmbError) as e:
         amb.amb_cell_index_noalloc(x, x, 1025, start, ids)
     assert e.value.status == amb.AMB_EINVAL
+
+
+def _random_xy(n, L, seed):
+    rng = np.random.default_rng(seed)
+    x = torch.from_numpy(rng.integers(0, L, n).astype(np.int32)).cuda()
+    y = torch.from_numpy(rng.integers(0, L, n).astype(np.int32)).cuda()
+    return x, y
+
+
+@pytest.mark.parametrize("n,L", [(0, 5), (0, 1), (1, 1), (37, 1), (1000, 2)])
+def test_noalloc_index_small_and_empty_cases(n, L):
+    x, y = _random_xy(n, L, 7 + n + L)
+    s_ref, i_ref = _index(amb.amb_cell_index, x, y, L, n)
+    s_new, i_new = _index(amb.amb_cell_index_noalloc, x, y, L, n)
+    assert np.array_equal(s_new, s_ref)
+    assert s_new[-1] == n
+    assert np.array_equal(_sorted_within_cells(s_new, i_new), _sorted_within_cells(s_ref, i_ref))
+
+
+def test_noalloc_index_reports_coordinates_outside_the_grid_and_recovers():
+    L, n = 40, 5000
+    x, y = _random_xy(n, L, 11)
+    x[17] = L  # one agent outside [0, L)
+    start = torch.empty(L * L + 1, dtype=torch.int32, device="cuda")
+    ids = torch.empty(n, dtype=torch.int32, device="cuda")
+    with pytest.raises(amb.AmbError) as e:
+        amb.amb_cell_index_noalloc(x, y, L, start, ids)
+    assert e.value.status == amb.AMB_EINVAL
+    assert int(start[-1]) == n - 1  # the agent is left out, as amb_cell_index does
+    # the next call starts from a clean error word
+    x[17] = 0
+    s_ref, i_ref = _index(amb.amb_cell_index, x, y, L, n)
+    s_new, i_new = _index(amb.amb_cell_index_noalloc, x, y, L, n)
+    assert np.array_equal(s_new, s_ref)
+    assert np.array_equal(_sorted_within_cells(s_new, i_new), _sorted_within_cells(s_ref, i_ref))
+
+
+def test_noalloc_index_rejects_a_misaligned_start_buffer():
+    L, n = 8, 10
+    x, y = _random_xy(n, L, 3)
+    buf = torch.empty(L * L + 2, dtype=torch.int32, device="cuda")
+    ids = torch.empty(n, dtype=torch.int32, device="cuda")
+    with pytest.raises(amb.AmbError) as e:
+        amb.amb_cell_index_noalloc(x, y, L, buf[1:], ids)  # 4 bytes past a 16-byte boundary
+    assert e.value.status == amb.AMB_EINVAL
+
+
+def test_noalloc_index_asynchronous_on_a_side_stream():
+    # sync = 0 on a non-default stream: the call only queues the work; after
+    # the stream is synchronised the result equals the allocating index
+    L, n = 300, 120_000
+    x, y = _random_xy(n, L, 19)
+    s_ref, i_ref = _index(amb.amb_cell_index, x, y, L, n)
+    side = torch.cuda.Stream()
+    start = torch.full((L * L + 1,), -1, dtype=torch.int32, device="cuda")
+    ids = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    for _ in range(2):  # twice in a row on the same stream
+        amb.amb_cell_index_noalloc(x, y, L, start, ids, stream=side, sync=False)
+    side.synchronize()
+    s_new, i_new = start.cpu().numpy(), ids.cpu().numpy()
+    assert np.array_equal(s_new, s_ref)
+    assert np.array_equal(_sorted_within_cells(s_new, i_new), _sorted_within_cells(s_ref, i_ref))
