@@ -273,9 +273,15 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s
 amb_status host_thresholds(double beta, double gamma, uint32_t cap, uint32_t *t_inf, uint32_t *K,
                            uint32_t *t_rec);
 
-inline unsigned grid_for(uint64_t work, unsigned per_block, unsigned cap = 152u * 64u)
+// Multiprocessor count of the current device (queried once per device).
+unsigned device_sms();
+
+// Blocks for `work` items at `per_block` per block, at most `per_sm` blocks
+// per multiprocessor of the current device.
+inline unsigned grid_for(uint64_t work, unsigned per_block, unsigned per_sm = 64u)
 {
     uint64_t g = (work + per_block - 1) / per_block;
+    const uint64_t cap = (uint64_t)device_sms() * per_sm;
     if (g < 1) g = 1;
     if (g > cap) g = cap;
     return (unsigned)g;

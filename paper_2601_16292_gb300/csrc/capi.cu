@@ -27,6 +27,23 @@ amb_status fail(amb_status st, const char *fmt, ...)
 
 void clear_error() { g_err[0] = 0; }
 
+unsigned device_sms()
+{
+    constexpr int kMaxDevices = 64;
+    static std::atomic<unsigned> cache[kMaxDevices];  // 0 = not queried yet
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = -1;
+    if (dev >= 0) {
+        const unsigned c = cache[dev].load(std::memory_order_relaxed);
+        if (c) return c;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev < 0 ? 0 : dev) != cudaSuccess || sms < 1)
+        sms = 1;
+    if (dev >= 0) cache[dev].store((unsigned)sms, std::memory_order_relaxed);
+    return (unsigned)sms;
+}
+
 // ------------------------------------------------------------ thresholds ---
 // Probability -> uint32 threshold: an event of probability p happens iff the
 // uniform 32-bit word is below min(floor(p * 2^32), 2^32 - 1).
@@ -179,7 +196,7 @@ static amb_status count_bad_i32(amb_pop *pop, const int32_t *v, uint32_t n, uint
     unsigned long long *bad = nullptr;
     AMB_TRY(dalloc(&bad, 1, pop->stream));
     cudaMemsetAsync(bad, 0, sizeof(*bad), pop->stream);
-    if (n) range_check_i32_kernel<<<grid_for(n, 256, 152u * 8u), 256, 0, pop->stream>>>(v, n, hi, bad);
+    if (n) range_check_i32_kernel<<<grid_for(n, 256, 8u), 256, 0, pop->stream>>>(v, n, hi, bad);
     cudaMemcpyAsync(h, bad, sizeof(*h), cudaMemcpyDeviceToHost, pop->stream);
     dfree(bad, pop->stream);
     AMB_TRY_CUDA(cudaStreamSynchronize(pop->stream));
@@ -191,7 +208,7 @@ static amb_status count_bad_u8(amb_pop *pop, const uint8_t *v, uint32_t n, uint3
     unsigned long long *bad = nullptr;
     AMB_TRY(dalloc(&bad, 1, pop->stream));
     cudaMemsetAsync(bad, 0, sizeof(*bad), pop->stream);
-    if (n) range_check_u8_kernel<<<grid_for(n, 256, 152u * 8u), 256, 0, pop->stream>>>(v, n, hi, bad);
+    if (n) range_check_u8_kernel<<<grid_for(n, 256, 8u), 256, 0, pop->stream>>>(v, n, hi, bad);
     cudaMemcpyAsync(h, bad, sizeof(*h), cudaMemcpyDeviceToHost, pop->stream);
     dfree(bad, pop->stream);
     AMB_TRY_CUDA(cudaStreamSynchronize(pop->stream));
@@ -407,7 +424,7 @@ amb_status amb_create(amb_model model, const amb_params *p, uint64_t seed, uint3
         CREATE_TRY(dalloc(&pop->err, 1, s));
         CREATE_CUDA(cudaMemsetAsync(pop->err, 0, sizeof(uint32_t), s));
         CREATE_TRY(ensure_series(pop, 64));
-        const unsigned g = grid_for(n, 256, 152u * 16u);
+        const unsigned g = grid_for(n, 256, 16u);
         if (model == AMB_WEALTH) {
             CREATE_TRY(dalloc(&pop->w, n, s));
             if (n) fill_i32_kernel<<<g, 256, 0, s>>>(pop->w, n, p->w_init);

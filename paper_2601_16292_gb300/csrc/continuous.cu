@@ -389,7 +389,7 @@ amb_status cont_init(amb_pop *pop)
         pop->init_infected = pop->cp.n_init_infected;
     }
     if (n)
-        cinit_kernel<<<grid_for(n, 256, 152u * 16u), 256, 0, s>>>(pop->fx, pop->fy, pop->state, pop->days, n,
+        cinit_kernel<<<grid_for(n, 256, 16u), 256, 0, s>>>(pop->fx, pop->fy, pop->state, pop->days, n,
                                                                   pop->cp.width, pop->cp.height,
                                                                   pop->cp.n_init_infected, pop->key0, pop->key1);
     AMB_TRY_CUDA(cudaGetLastError());
@@ -403,7 +403,7 @@ amb_status cont_steps(amb_pop *pop, uint32_t k)
     const uint32_t n = p.n;
     int64_t *rows = pop->series + (size_t)pop->t * 4u;
     if (pop->model == AMB_CWALK) {
-        cwalk_kernel<<<grid_for(n, 256, 152u * 32u), 256, 0, s>>>(pop->fx, pop->fy, n, p.width, p.height, p.step,
+        cwalk_kernel<<<grid_for(n, 256, 32u), 256, 0, s>>>(pop->fx, pop->fy, n, p.width, p.height, p.step,
                                                                   pop->key0, pop->key1, (uint32_t)pop->t, k, rows);
         AMB_TRY_CUDA(cudaGetLastError());
         pop->launches += 1;
@@ -425,7 +425,7 @@ amb_status cont_steps(amb_pop *pop, uint32_t k)
         return AMB_OK;
     }
     AMB_TRY_CUDA(cudaMemsetAsync(rows, 0, (size_t)k * 4u * sizeof(int64_t), s));
-    const unsigned grid = grid_for(n, 256, 152u * 16u);
+    const unsigned grid = grid_for(n, 256, 16u);
     for (uint32_t j = 0; j < k; ++j) {
         const uint32_t t = (uint32_t)(pop->t + j);
         AMB_TRY_CUDA(cudaMemsetAsync(pop->cnt, 0, (size_t)C * sizeof(int32_t), s));
@@ -486,7 +486,7 @@ amb_status cont_write_column(amb_pop *pop, amb_col col, const void *src, size_t 
             cudaSuccess)
         st = fail(AMB_ECUDA, "column upload failed");
     if (st == AMB_OK && n) {
-        const unsigned g = grid_for(n, 256, 152u * 8u);
+        const unsigned g = grid_for(n, 256, 8u);
         if (col == AMB_COL_X || col == AMB_COL_Y)
             cbounds_kernel<<<g, 256, 0, s>>>(reinterpret_cast<const float *>(tmp), (uint32_t)n,
                                              col == AMB_COL_X ? pop->cp.width : pop->cp.height, bad);
@@ -520,7 +520,7 @@ amb_status cont_bounds(amb_pop *pop, bool *ok)
     AMB_TRY_CUDA(cudaMemsetAsync(bad, 0, sizeof(*bad), s));
     const uint32_t n = pop->cp.n;
     if (n) {
-        const unsigned g = grid_for(n, 256, 152u * 8u);
+        const unsigned g = grid_for(n, 256, 8u);
         cbounds_kernel<<<g, 256, 0, s>>>(pop->fx, n, pop->cp.width, bad);
         cbounds_kernel<<<g, 256, 0, s>>>(pop->fy, n, pop->cp.height, bad);
     }

@@ -109,9 +109,7 @@ amb_status launch_scan(const int32_t *in, int32_t *out, int32_t *out2, uint32_t 
     AMB_TRY(lb.ensure(n_tiles, s));
     uint32_t parity, epoch;
     lb.next(&parity, &epoch);
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned sms = device_sms();
     const unsigned grid = (unsigned)std::min<uint64_t>(n_tiles, (uint64_t)sms * 8u);
     scan_kernel<<<grid, kScanNT, 0, s>>>(in, out, out2, m, n_tiles, lb.tickets, parity, lb.status, epoch, err);
     AMB_TRY_CUDA(cudaGetLastError());
@@ -166,9 +164,7 @@ amb_status launch_cell_index_raw(const int32_t *x, const int32_t *y, uint32_t n,
         cell_hist_kernel<<<grid_for(n, 256), 256, 0, s>>>(x, y, n, (int32_t)L, cnt, err);
         AMB_TRY_CUDA(cudaGetLastError());
     }
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned sms = device_sms();
     const unsigned grid = (unsigned)std::min<uint64_t>(n_tiles, (uint64_t)sms * 8u);
     scan_kernel<<<grid, kScanNT, 0, s>>>(cnt, start, cursor, (uint32_t)C, n_tiles, tickets, parity, status, epoch, err);
     AMB_TRY_CUDA(cudaGetLastError());

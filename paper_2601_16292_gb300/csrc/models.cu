@@ -48,7 +48,7 @@ amb_status walk_steps(amb_pop *pop, uint32_t k)
 {
     const uint32_t n = pop->p.n;
     if (k == 0) return AMB_OK;
-    walk_kernel<<<grid_for(n, 256, 152u * 32u), 256, 0, pop->stream>>>(
+    walk_kernel<<<grid_for(n, 256, 32u), 256, 0, pop->stream>>>(
         pop->x, pop->y, n, (int32_t)pop->p.grid_side, pop->key0, pop->key1, (uint32_t)pop->t, k, pop->err,
         pop->series + (size_t)pop->t * 4u);
     AMB_TRY_CUDA(cudaGetLastError());
@@ -384,7 +384,7 @@ amb_status wealth_steps(amb_pop *pop, uint32_t k)
         pop->launches += 1;
         return AMB_OK;
     }
-    const unsigned g = grid_for(n, 256, 152u * 16u);
+    const unsigned g = grid_for(n, 256, 16u);
     for (uint32_t s = 0; s < k; ++s) {
         int64_t *row = rows + (size_t)s * 4u;
         if (n >= 2) {
@@ -479,7 +479,7 @@ amb_status sir_generic_steps(amb_pop *pop, uint32_t k)
     int64_t *rows = pop->series + (size_t)pop->t * 4u;
     if (k == 0) return AMB_OK;
     AMB_TRY_CUDA(cudaMemsetAsync(rows, 0, (size_t)k * 4u * sizeof(int64_t), pop->stream));
-    const unsigned g = grid_for(n, 256, 152u * 16u);
+    const unsigned g = grid_for(n, 256, 16u);
     for (uint32_t s = 0; s < k; ++s) {
         const uint32_t t = (uint32_t)(pop->t + s);
         AMB_TRY_CUDA(cudaMemsetAsync(pop->cnt, 0, C * sizeof(int32_t), pop->stream));

@@ -825,9 +825,7 @@ __global__ void band_read_kernel(const uint2 *__restrict__ rec, const int32_t *_
 
 static int sm_count()
 {
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned sms = device_sms();
     return sms;
 }
 
@@ -928,7 +926,7 @@ amb_status sir_band_init(amb_pop *pop, const int32_t *x, const int32_t *y, const
         b.t_inf = pop->t_inf_d;
         b.K = pop->K;
         b.t_rec = pop->t_rec;
-        band_build_kernel<<<grid_for(n, 256, 152u * 8u), 256, 0, s>>>(b);
+        band_build_kernel<<<grid_for(n, 256, 8u), 256, 0, s>>>(b);
     }
     dfree(ids, s);
     AMB_TRY_CUDA(cudaGetLastError());
@@ -990,7 +988,7 @@ amb_status sir_band_read(amb_pop *pop, amb_col col, void *dst_dev)
 {
     const uint32_t n = pop->p.n;
     if (n == 0) return AMB_OK;
-    band_read_kernel<<<grid_for(n, 256, 152u * 8u), 256, 0, pop->stream>>>(
+    band_read_kernel<<<grid_for(n, 256, 8u), 256, 0, pop->stream>>>(
         pop->rec[pop->cur], pop->row_start[pop->cur], pop->start, n, pop->p.grid_side, (int)col, dst_dev);
     AMB_TRY_CUDA(cudaGetLastError());
     return AMB_OK;

@@ -223,7 +223,7 @@ amb_status launch_minmax_sum(const int32_t *v, uint32_t n, int32_t *mm, unsigned
     const int32_t init[2] = {INT32_MAX, INT32_MIN};
     AMB_TRY_CUDA(cudaMemcpyAsync(mm, init, sizeof(init), cudaMemcpyHostToDevice, s));
     AMB_TRY_CUDA(cudaMemsetAsync(sum, 0, sizeof(unsigned long long), s));
-    if (n) minmax_sum_kernel<<<grid_for(n, 256, 152u * 8u), 256, 0, s>>>(v, n, mm, sum);
+    if (n) minmax_sum_kernel<<<grid_for(n, 256, 8u), 256, 0, s>>>(v, n, mm, sum);
     AMB_TRY_CUDA(cudaGetLastError());
     return AMB_OK;
 }
@@ -232,7 +232,7 @@ amb_status launch_value_hist(const int32_t *v, uint32_t n, int32_t base, uint32_
                              cudaStream_t s)
 {
     AMB_TRY_CUDA(cudaMemsetAsync(hist, 0, (size_t)bins * sizeof(unsigned long long), s));
-    if (n) value_hist_kernel<<<grid_for(n, 256, 152u * 8u), 256, 0, s>>>(v, n, base, bins, hist);
+    if (n) value_hist_kernel<<<grid_for(n, 256, 8u), 256, 0, s>>>(v, n, base, bins, hist);
     AMB_TRY_CUDA(cudaGetLastError());
     return AMB_OK;
 }
@@ -249,14 +249,14 @@ amb_status launch_occupancy(const int32_t *x, const int32_t *y, uint32_t n, uint
 {
     const uint64_t C = (uint64_t)L * L;
     AMB_TRY_CUDA(cudaMemsetAsync(occ, 0, C * sizeof(int32_t), s));
-    if (n) occupancy_kernel<<<grid_for(n, 256, 152u * 8u), 256, 0, s>>>(x, y, n, (int32_t)L, occ);
+    if (n) occupancy_kernel<<<grid_for(n, 256, 8u), 256, 0, s>>>(x, y, n, (int32_t)L, occ);
     AMB_TRY_CUDA(cudaGetLastError());
     return AMB_OK;
 }
 
 amb_status launch_occupancy_from_start(const int32_t *start, uint64_t C, int32_t *occ, cudaStream_t s)
 {
-    occupancy_from_start_kernel<<<grid_for(C, 256, 152u * 8u), 256, 0, s>>>(start, C, occ);
+    occupancy_from_start_kernel<<<grid_for(C, 256, 8u), 256, 0, s>>>(start, C, occ);
     AMB_TRY_CUDA(cudaGetLastError());
     return AMB_OK;
 }
@@ -265,7 +265,7 @@ amb_status launch_max(const int32_t *v, uint64_t m, int32_t *out, cudaStream_t s
 {
     const int32_t init = INT32_MIN;
     AMB_TRY_CUDA(cudaMemcpyAsync(out, &init, sizeof(init), cudaMemcpyHostToDevice, s));
-    if (m) max_kernel<<<grid_for(m, 256, 152u * 8u), 256, 0, s>>>(v, m, out);
+    if (m) max_kernel<<<grid_for(m, 256, 8u), 256, 0, s>>>(v, m, out);
     AMB_TRY_CUDA(cudaGetLastError());
     return AMB_OK;
 }
@@ -273,7 +273,7 @@ amb_status launch_max(const int32_t *v, uint64_t m, int32_t *out, cudaStream_t s
 amb_status launch_count_hist(const int32_t *v, uint64_t m, uint32_t bins, unsigned long long *hist, cudaStream_t s)
 {
     AMB_TRY_CUDA(cudaMemsetAsync(hist, 0, (size_t)bins * sizeof(unsigned long long), s));
-    if (m) count_hist_kernel<<<grid_for(m, 256, 152u * 8u), 256, 0, s>>>(v, m, bins, hist);
+    if (m) count_hist_kernel<<<grid_for(m, 256, 8u), 256, 0, s>>>(v, m, bins, hist);
     AMB_TRY_CUDA(cudaGetLastError());
     return AMB_OK;
 }
@@ -288,14 +288,14 @@ amb_status launch_curve_sums(const int64_t *series, uint32_t T, long long *out, 
 amb_status launch_bounds_check(const int32_t *x, const int32_t *y, uint32_t n, uint32_t L, unsigned long long *bad,
                                cudaStream_t s)
 {
-    if (n) bounds_check_kernel<<<grid_for(n, 256, 152u * 8u), 256, 0, s>>>(x, y, n, (int32_t)L, bad);
+    if (n) bounds_check_kernel<<<grid_for(n, 256, 8u), 256, 0, s>>>(x, y, n, (int32_t)L, bad);
     AMB_TRY_CUDA(cudaGetLastError());
     return AMB_OK;
 }
 
 amb_status launch_monotone_check(const int32_t *start, uint64_t C, unsigned long long *bad, cudaStream_t s)
 {
-    if (C) monotone_check_kernel<<<grid_for(C, 256, 152u * 8u), 256, 0, s>>>(start, C, bad);
+    if (C) monotone_check_kernel<<<grid_for(C, 256, 8u), 256, 0, s>>>(start, C, bad);
     AMB_TRY_CUDA(cudaGetLastError());
     return AMB_OK;
 }
@@ -303,7 +303,7 @@ amb_status launch_monotone_check(const int32_t *start, uint64_t C, unsigned long
 amb_status launch_state_count(const uint8_t *st, uint32_t n, unsigned long long *cnt, cudaStream_t s)
 {
     AMB_TRY_CUDA(cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned long long), s));
-    if (n) state_count_kernel<<<grid_for(n, 256, 152u * 8u), 256, 0, s>>>(st, n, cnt);
+    if (n) state_count_kernel<<<grid_for(n, 256, 8u), 256, 0, s>>>(st, n, cnt);
     AMB_TRY_CUDA(cudaGetLastError());
     return AMB_OK;
 }

@@ -683,7 +683,7 @@ __global__ void __launch_bounds__(256) grid_walk_kernel(GridWalkArgs a, uint32_t
 
 unsigned map_grid(uint64_t work)
 {
-    return grid_for(work, kMapNT, 152u * 16u);
+    return grid_for(work, kMapNT, 16u);
 }
 
 // ----------------------------------------------------------- dispatch ---
@@ -953,7 +953,7 @@ amb_status amb_table_add_column(amb_table *t, const char *name, amb_dtype dtype,
         word = b | (b << 8) | (b << 16) | (b << 24);
     }
     if (bytes) {
-        fill_kernel<<<grid_for(bytes / 4u, 256, 152u * 8u), 256, 0, t->stream>>>(p, bytes, word);
+        fill_kernel<<<grid_for(bytes / 4u, 256, 8u), 256, 0, t->stream>>>(p, bytes, word);
         if (cudaGetLastError() != cudaSuccess) {
             dfree(c.ptr, t->stream);
             return fail(AMB_ECUDA, "fill launch failed");
@@ -1084,7 +1084,7 @@ amb_status amb_view_from_ids(amb_table *t, const int32_t *ids, size_t k, int ids
     if (st == AMB_OK && cudaMemcpyAsync(v->count, &kk, sizeof(kk), cudaMemcpyHostToDevice, t->stream) != cudaSuccess)
         st = fail(AMB_ECUDA, "count copy failed");
     if (st == AMB_OK && ids_on_device && k) {
-        ids_check_kernel<<<grid_for(k, 256, 152u * 8u), 256, 0, t->stream>>>(v->ids, kk, t->n, t->err);
+        ids_check_kernel<<<grid_for(k, 256, 8u), 256, 0, t->stream>>>(v->ids, kk, t->n, t->err);
         if (cudaGetLastError() != cudaSuccess) st = fail(AMB_ECUDA, "check launch failed");
     }
     if (st == AMB_OK) st = table_error(t);  // also: the host copies are complete
@@ -1266,10 +1266,10 @@ amb_status amb_log_record(amb_log *l, int col, const int32_t *ids, const int64_t
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     AMB_TRY_CUDA(cudaMemcpyAsync(l->ids + l->count, ids, k * sizeof(int32_t), kind, s));
     AMB_TRY_CUDA(cudaMemcpyAsync(l->vals + l->count, values, k * sizeof(int64_t), kind, s));
-    fill_i32_kernel<<<grid_for(k, 256, 152u * 8u), 256, 0, s>>>(l->cols + l->count, (uint32_t)k, col);
+    fill_i32_kernel<<<grid_for(k, 256, 8u), 256, 0, s>>>(l->cols + l->count, (uint32_t)k, col);
     AMB_TRY_CUDA(cudaGetLastError());
     if (on_device) {
-        ids_check_kernel<<<grid_for(k, 256, 152u * 8u), 256, 0, s>>>(l->ids + l->count, (uint32_t)k, t->n, t->err);
+        ids_check_kernel<<<grid_for(k, 256, 8u), 256, 0, s>>>(l->ids + l->count, (uint32_t)k, t->n, t->err);
         AMB_TRY_CUDA(cudaGetLastError());
         AMB_TRY(table_error(t));  // a bad id leaves the log unchanged (count not advanced)
     } else {
@@ -1314,7 +1314,7 @@ amb_status amb_log_flush(amb_log *l)
         }
         lc.win[c] = l->win[c];
     }
-    const unsigned g = grid_for(l->count, 256, 152u * 16u);
+    const unsigned g = grid_for(l->count, 256, 16u);
     log_claim_kernel<<<g, 256, 0, s>>>(l->ids, l->cols, l->count, l->base, lc);
     log_apply_kernel<<<g, 256, 0, s>>>(l->ids, l->cols, l->vals, l->count, l->base, lc);
     AMB_TRY_CUDA(cudaGetLastError());
@@ -1375,7 +1375,7 @@ amb_status amb_table_grid_walk(amb_table *t, const int *cols, uint32_t d, const 
     a.steps = steps;
     a.moore = moore != 0;
     a.torus = torus != 0;
-    const unsigned g = grid_for(t->n, 256, 152u * 32u);
+    const unsigned g = grid_for(t->n, 256, 32u);
 #define GW_CASE(D)                                                                                 \
     case D:                                                                                        \
         if (a.moore && a.torus) grid_walk_kernel<D, true, true><<<g, 256, 0, t->stream>>>(a, t->err);   \

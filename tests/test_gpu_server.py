@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle_jobs import oracle_pool, stratified, submit_oracle_jobs
 from paper_2601_16292_gb300 import amb, workloads
 
 pytestmark = pytest.mark.gpu
@@ -184,17 +185,26 @@ def test_cancel_queued_and_running_jobs(stream):
 
 
 def test_serving_trace_sample_equals_oracle(stream):
-    """Jobs of the serving trace (sizes capped at 20,000 agents so that the
-    oracle stays quick) served together, each equal to the oracle."""
-    jobs = workloads.scaled(workloads.serve_trace(n_jobs=30)[1], 20_000)
-    srv = amb.Server(RESERVE + (1 << 30), stream, chunk_steps=16)
-    tickets = [srv.submit(j, keep_columns=True) for j in jobs]
-    srv.drain(300.0)
-    for t, j in zip(tickets, jobs):
-        kw = {k: v for k, v in j.items() if k not in ("model", "steps")}
-        o = oracle.Population(j["model"], **kw).step(j["steps"])
-        assert np.array_equal(srv.counts(t), o.counts()), j
-        cols = ("wealth",) if j["model"] == "wealth" else (("x", "y", "state") if j["model"] == "sir" else ("x", "y"))
-        for c in cols:
-            assert np.array_equal(srv.column(t, c), getattr(o, "w" if c == "wealth" else c)), (j, c)
-    srv.close()
+    """50 jobs of the 5,000-job serving trace at their own sizes and lengths
+    (up to 4 million agents and 500 steps; 17 wealth, 17 walk and 16 SIR jobs
+    evenly spaced by size rank, the smallest and the largest of each model
+    included), submitted to one server together: each job's count series and
+    final columns equal the oracle's run of that job."""
+    trace = workloads.serve_trace()[1]
+    sample = stratified(trace, {"wealth": 17, "walk": 17, "sir": 16})
+    assert len(sample) == 50
+    jobs = [trace[i] for i in sample]
+    with oracle_pool(len(jobs)) as pool:
+        futs = submit_oracle_jobs(jobs, pool)
+        srv = amb.Server(RESERVE + (64 << 30), stream, chunk_steps=32)
+        tickets = [srv.submit(j, keep_columns=True) for j in jobs]
+        srv.drain(600.0)
+        for t, j, f in zip(tickets, jobs, futs):
+            assert srv.poll(t)["status"] == amb.AMB_OK, j
+            o = f.result()
+            assert np.array_equal(srv.counts(t), o.counts()), j
+            cols = ("wealth",) if j["model"] == "wealth" else (("x", "y", "state") if j["model"] == "sir" else ("x", "y"))
+            for c in cols:
+                assert np.array_equal(srv.column(t, c), getattr(o, "w" if c == "wealth" else c)), (j, c)
+            srv.release(t)
+        srv.close()

@@ -1,11 +1,13 @@
 """The parameter sweep (1,024 wealth and SIR replicates of uneven size, 200
-steps each) advanced as one batch: a stratified sample of the jobs equals the
-oracle bit for bit, every job keeps the models' invariants in its per-step
-counts, and the largest jobs equal a lone run of the same job."""
+steps each) advanced as one batch: a stratified sample of 32 jobs (16 per
+model, evenly spaced by size rank, the smallest and the largest included, up
+to 10^6 agents at full length) equals the oracle bit for bit, every job keeps
+the models' invariants in its per-step counts, and the largest jobs equal a
+lone run of the same job."""
 import numpy as np
 import pytest
 
-import oracle
+from oracle_jobs import oracle_pool, stratified, submit_oracle_jobs
 from paper_2601_16292_gb300 import amb, workloads
 
 pytestmark = pytest.mark.gpu
@@ -25,32 +27,25 @@ def sweep():
     b.close()
 
 
-def _sample(jobs, per_model=5, max_n=120_000):
-    """Smallest, largest (up to max_n) and evenly spaced sizes of each model."""
-    out = []
-    for model in ("wealth", "sir"):
-        idx = sorted((i for i, j in enumerate(jobs) if j["model"] == model and j["n"] <= max_n),
-                     key=lambda i: jobs[i]["n"])
-        pick = np.linspace(0, len(idx) - 1, per_model).round().astype(int)
-        out += [idx[p] for p in pick]
-    return out
-
-
 def test_sweep_sample_equals_oracle(sweep):
     jobs, b, _ = sweep
-    for i in _sample(jobs):
-        j = jobs[i]
-        kw = {k: v for k, v in j.items() if k not in ("model", "steps")}
-        o = oracle.Population(j["model"], **kw).step(j["steps"])
-        v = b.population(i)
-        assert v.t == j["steps"]
-        assert np.array_equal(v.counts(), o.counts()), i
-        if j["model"] == "wealth":
-            assert np.array_equal(v.column("wealth").cpu().numpy(), o.w), i
-        else:
-            assert np.array_equal(v.column("state").cpu().numpy(), o.state), i
-            assert np.array_equal(v.column("x").cpu().numpy(), o.x), i
-            assert np.array_equal(v.column("y").cpu().numpy(), o.y), i
+    sample = stratified(jobs, {"wealth": 16, "sir": 16})
+    assert len(sample) == 32
+    assert max(jobs[i]["n"] for i in sample) == max(j["n"] for j in jobs)
+    with oracle_pool(len(sample)) as pool:
+        futs = submit_oracle_jobs([jobs[i] for i in sample], pool)
+        for i, f in zip(sample, futs):
+            j = jobs[i]
+            o = f.result()
+            v = b.population(i)
+            assert v.t == j["steps"]
+            assert np.array_equal(v.counts(), o.counts()), i
+            if j["model"] == "wealth":
+                assert np.array_equal(v.column("wealth").cpu().numpy(), o.w), i
+            else:
+                assert np.array_equal(v.column("state").cpu().numpy(), o.state), i
+                assert np.array_equal(v.column("x").cpu().numpy(), o.x), i
+                assert np.array_equal(v.column("y").cpu().numpy(), o.y), i
 
 
 def test_sweep_invariants_every_job(sweep):
