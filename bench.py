@@ -344,41 +344,55 @@ def _latency_summary(lat, total, span):
             "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()), "max_s": float(lat.max())}
 
 
-def serve_bench(amb, torch, stream, rank, world, n_jobs=5000, chunk=32, budget_gb=120):
+def serve_bench(amb, torch, stream, rank, world, n_jobs=5000, chunk=32, budget_gb=120, rates=(200.0, 400.0, 800.0),
+                iteration_us=None):
     """The serving trace (5,000 jobs, Poisson arrivals at 200/s; ranks split the
-    trace) replayed in real time: served by the continuous-batching loop under a
-    120 GB budget, and by one-at-a-time stepping through the plain API (each job
-    created, stepped, its counts read, destroyed; a job starts when it has
-    arrived and the previous one is done).  Latency = arrival to result read."""
+    trace), replayed in real time at its own rate and with its arrival times
+    compressed to 400 and 800 jobs/s (the same jobs in the same order): served
+    by the continuous-batching loop under a 120 GB budget, and by one-at-a-time
+    stepping through the plain API (each job created, stepped, its counts read,
+    destroyed; a job starts when it has arrived and the previous one is done).
+    Also every job queued at t = 0 (capacity).  Latency = arrival to result
+    read.  Every served job's count rows must equal the same job's rows run
+    alone (the run raises otherwise)."""
+    import numpy as np
     from paper_2601_16292_gb300 import workloads
     arrivals, jobs = workloads.serve_trace(n_jobs=n_jobs)
     arrivals, jobs = partition(arrivals, rank, world), partition(jobs, rank, world)
+    arrivals = np.asarray(arrivals, dtype=np.float64)
     total = workloads.agent_steps(jobs)
-    srv = amb.Server(int(budget_gb * 1e9), stream, chunk_steps=chunk)
-    # warm the worker's code paths on a few throwaway jobs
-    for j in workloads.scaled(jobs[:6], 20_000):
-        srv.submit(j)
-    srv.drain(120.0)
-    base = srv.stats()
-    tickets = []
-    t0 = time.perf_counter()
-    for a, j in zip(arrivals, jobs):
-        d = a - (time.perf_counter() - t0)
-        if d > 0:
-            time.sleep(d)
-        tickets.append(srv.submit(j))
-    srv.drain(3600.0)
-    res = [srv.poll(t) for t in tickets]
-    served_counts = [srv.counts(t) for t in tickets]
-    st = srv.stats()
-    srv.close()
-    first = min(r["submit_s"] for r in res)
-    served = _latency_summary([r["done_s"] - r["submit_s"] for r in res], total,
-                              max(r["done_s"] for r in res) - first)
-    served.update({"iterations": st["iterations"] - base["iterations"], "launches": st["launches"] - base["launches"],
-                   "hbm_peak_gb": st["hbm_peak"] / 1e9, "chunk_steps": chunk,
-                   "failed": st["failed"] - base["failed"], "busy_s": st["busy_s"] - base["busy_s"]})
-    # one job at a time on the same trace
+    cfg = dict(chunk_steps=chunk)
+    if iteration_us is not None:
+        cfg["iteration_us"] = iteration_us
+
+    def served_run(arr, warm=False):
+        srv = amb.Server(int(budget_gb * 1e9), stream, **cfg)
+        if warm:  # the worker's code paths, on a few throwaway jobs
+            for j in workloads.scaled(jobs[:6], 20_000):
+                srv.submit(j)
+            srv.drain(120.0)
+        base = srv.stats()
+        tickets = []
+        t0 = time.perf_counter()
+        for a, j in zip(arr, jobs):
+            d = a - (time.perf_counter() - t0)
+            if d > 0:
+                time.sleep(d)
+            tickets.append(srv.submit(j))
+        srv.drain(3600.0)
+        res = [srv.poll(t) for t in tickets]
+        counts = [srv.counts(t) for t in tickets]
+        st = srv.stats()
+        srv.close()
+        if any(r["status"] != amb.AMB_OK for r in res):
+            raise RuntimeError("served jobs failed")
+        first = min(r["submit_s"] for r in res)
+        out = _latency_summary([r["done_s"] - r["submit_s"] for r in res], total,
+                               max(r["done_s"] for r in res) - first)
+        out.update({"iterations": st["iterations"] - base["iterations"], "launches": st["launches"] - base["launches"],
+                    "hbm_peak_gb": st["hbm_peak"] / 1e9, "busy_s": st["busy_s"] - base["busy_s"]})
+        return out, counts
+
     def one_at_a_time(arr, keep=None):
         lat = []
         torch.cuda.synchronize()
@@ -397,32 +411,35 @@ def serve_bench(amb, torch, stream, rank, world, n_jobs=5000, chunk=32, budget_g
                 keep.append(c)
         return _latency_summary(lat, total, time.perf_counter() - t0 - arr[0])
 
-    alone_counts = []
-    one = one_at_a_time(arrivals, alone_counts)
-    # every served job's per-step count rows equal the same job run alone
-    mismatched = [i for i, (a, b) in enumerate(zip(served_counts, alone_counts)) if not np.array_equal(a, b)]
-    if any(r["status"] != amb.AMB_OK for r in res) or mismatched:
-        raise RuntimeError("served results differ from one-at-a-time results: jobs %s" % mismatched[:10])
-    # capacity: every job queued at t = 0
-    srv = amb.Server(int(budget_gb * 1e9), stream, chunk_steps=chunk)
-    t0 = time.perf_counter()
-    tickets = [srv.submit(j) for j in jobs]
-    srv.drain(3600.0)
-    res = [srv.poll(t) for t in tickets]
-    sat_mismatched = [i for i, t in enumerate(tickets) if not np.array_equal(srv.counts(t), alone_counts[i])]
-    srv.close()
-    if any(r["status"] != amb.AMB_OK for r in res) or sat_mismatched:
-        raise RuntimeError("served results differ from one-at-a-time results: jobs %s" % sat_mismatched[:10])
-    sat_served = _latency_summary([r["done_s"] - r["submit_s"] for r in res], total,
-                                  max(r["done_s"] for r in res) - min(r["submit_s"] for r in res))
-    sat_one = one_at_a_time([0.0] * len(jobs))
-    return {"jobs": len(jobs), "agent_steps": total, "arrival_rate_per_s": 200.0 / world,
-            "budget_gb": budget_gb, "offered_load": total / float(arrivals[-1] - arrivals[0]),
-            "trace": {"served": served, "one_at_a_time": one},
-            "results_equal_alone": {"jobs_checked": len(jobs), "runs": ["trace", "saturated"],
-                                    "what": "every job's per-step count rows, served vs one at a time"},
+    def check(counts, alone):
+        bad = [i for i, (a, b) in enumerate(zip(counts, alone)) if not np.array_equal(a, b)]
+        if bad:
+            raise RuntimeError("served results differ from one-at-a-time results: jobs %s" % bad[:10])
+
+    by_rate = {}
+    alone = []
+    for k, rate in enumerate(rates):
+        arr = arrivals * (200.0 / rate)
+        served, counts = served_run(arr, warm=(k == 0))
+        one = one_at_a_time(arr, alone if k == 0 else None)
+        check(counts, alone)
+        by_rate["%g" % (rate / world)] = {"served": served, "one_at_a_time": one,
+                                          "offered_load": total / float(arr[-1] - arr[0]),
+                                          "served_keeps_up": bool(served["makespan_s"] <= 1.1 * float(arr[-1] - arr[0])),
+                                          "one_at_a_time_keeps_up":
+                                              bool(one["makespan_s"] <= 1.1 * float(arr[-1] - arr[0]))}
+    zero = np.zeros_like(arrivals)
+    sat_served, counts = served_run(zero)
+    check(counts, alone)
+    sat_one = one_at_a_time(zero)
+    base_key = "%g" % (rates[0] / world)
+    return {"jobs": len(jobs), "agent_steps": total, "arrival_rate_per_s": rates[0] / world,
+            "budget_gb": budget_gb, "chunk_steps": chunk, "offered_load": by_rate[base_key]["offered_load"],
+            "trace": by_rate[base_key], "by_arrival_rate": by_rate,
             "saturated": {"served": sat_served, "one_at_a_time": sat_one,
                           "speedup_throughput": sat_served["value"] / sat_one["value"]},
+            "results_equal_alone": {"jobs_checked": len(jobs), "runs": len(rates) + 1,
+                                    "what": "every job's per-step count rows, served vs one at a time"},
             "unit": "agent-steps/s"}
 
 

@@ -352,7 +352,10 @@ amb_status amb_job_bytes(const amb_job *job, size_t *resident, size_t *transient
  * the device, and advances all admitted jobs together, chunk_steps steps at a
  * time, with the batched launches (continuous batching: jobs that arrive
  * while others run join at the next chunk; finished jobs leave and free their
- * memory).  A job's results are bit-identical to stepping it alone.
+ * memory).  An iteration also ends at the step where the first of its jobs
+ * finishes (it takes at least min(8, chunk_steps) steps), so a finished job's
+ * result does not wait for the others' chunks.  A job's results are
+ * bit-identical to stepping it alone.
  */
 typedef struct {
     size_t hbm_budget_bytes; /* device memory for job state (resident + the creation
@@ -363,6 +366,11 @@ typedef struct {
     int32_t spread_bands;    /* 0: per iteration, spread the bands over every SM when
                                 the active SIR jobs' fewest bands would leave SMs idle;
                                 1: always spread; -1: always the fewest bands */
+    uint32_t iteration_us;   /* 0: no time target; otherwise an iteration takes at most
+                                as many steps as the previous iteration's device time per
+                                step says fit in this many microseconds (at least
+                                min(8, chunk_steps)), so that jobs arriving meanwhile
+                                join sooner */
 } amb_server_config;
 
 typedef struct {

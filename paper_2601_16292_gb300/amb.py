@@ -77,7 +77,8 @@ class amb_batch_report(ctypes.Structure):
 
 class amb_server_config(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_active", ctypes.c_uint32),
-                ("chunk_steps", ctypes.c_uint32), ("band_rows_cap", ctypes.c_uint32), ("spread_bands", ctypes.c_int32)]
+                ("chunk_steps", ctypes.c_uint32), ("band_rows_cap", ctypes.c_uint32), ("spread_bands", ctypes.c_int32),
+                ("iteration_us", ctypes.c_uint32)]
 
 
 class amb_result(ctypes.Structure):
@@ -413,10 +414,11 @@ def _result_dict(r):
             "last": list(r.last), "submit_s": r.submit_s, "admit_s": r.admit_s, "done_s": r.done_s}
 
 
-def amb_server_create(hbm_budget_bytes, stream, max_active=0, chunk_steps=0, band_rows_cap=0, spread_bands=0):
+def amb_server_create(hbm_budget_bytes, stream, max_active=0, chunk_steps=0, band_rows_cap=0, spread_bands=0,
+                      iteration_us=0):
     cfg = amb_server_config(hbm_budget_bytes=int(hbm_budget_bytes), max_active=int(max_active),
                             chunk_steps=int(chunk_steps), band_rows_cap=int(band_rows_cap),
-                            spread_bands=int(spread_bands))
+                            spread_bands=int(spread_bands), iteration_us=int(iteration_us))
     h = ctypes.c_void_p()
     _check(lib().amb_server_create(ctypes.byref(cfg), _stream_handle(stream), ctypes.byref(h)))
     return h

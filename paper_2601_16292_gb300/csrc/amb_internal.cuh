@@ -99,47 +99,24 @@ amb_status launch_cell_index_raw(const int32_t *x, const int32_t *y, uint32_t n,
 // ids[cursor[c]++] = i for every agent i in range (cursor = copy of start).
 amb_status launch_cell_scatter(const int32_t *x, const int32_t *y, uint32_t n, uint32_t L, int32_t *cursor,
                                int32_t *ids, cudaStream_t s);
-// ---- batches: many populations advanced by shared launches ----
-// Wealth populations: the small ones (column fits one CTA's shared memory)
-// run all their steps in one launch, one CTA per population; the large ones
-// take three launches per step over the concatenation of their columns.
-struct WealthBatch {
-    void *d_jobs = nullptr;
-    uint32_t *d_small = nullptr, *d_large = nullptr, *d_prefix = nullptr;
-    uint32_t n_jobs = 0, n_small = 0, n_large = 0, large_chunks = 0;
-    size_t smem = 0;
-};
+// ---- batches: many populations advanced by one persistent launch ----
 bool wealth_uses_smem(uint32_t n);
-amb_status wealth_batch_build(WealthBatch &wb, amb_pop **pops, const uint32_t *steps, uint32_t n, cudaStream_t s);
-amb_status wealth_batch_small(WealthBatch &wb, cudaStream_t s, uint64_t *launches);
-amb_status wealth_batch_large_step(WealthBatch &wb, cudaStream_t s, uint64_t *launches);
-void wealth_batch_release(WealthBatch &wb, cudaStream_t s);
-
-// SIR populations on the band path: one launch per step covers the bands of
-// every population (plus one small launch that advances their steps).
-struct SirBatch {
-    void *d_jobs = nullptr;
-    uint32_t *d_prefix = nullptr, *d_codes = nullptr, *wide = nullptr;
-    unsigned long long *tickets = nullptr;
-    uint32_t n_jobs = 0, total_bands = 0, grid = 0, wide_words = 0;
-    uint32_t epoch_base = 0, launches = 0;
-    size_t smem = 0;
-};
-// Band shape of the populations in a batch: rows per band at most rows_cap;
-// spread = as many bands as fill the GPU, else the fewest bands.
+// Band shape of the SIR populations of a batch: rows per band at most
+// rows_cap; spread = as many bands as fill the GPU, else the fewest bands.
 struct BandShape {
     uint32_t rows_cap = 32;
     bool spread = false;
     // adaptive: spread when the fewest bands of all live populations would
     // not give every SM two bands, else fewest
     bool adaptive = false;
+    // bytes of shared-memory counters a band may use (0: the single-population
+    // kernel's budget)
+    uint32_t smem_cap = 0;
 };
-amb_status sir_batch_build(SirBatch &sb, amb_pop **pops, const uint32_t *steps, uint32_t n, BandShape shape,
-                           cudaStream_t s);
-amb_status sir_batch_step(SirBatch &sb, cudaStream_t s, uint64_t *launches);
-// hand the populations back to single stepping after `steps[q]` batched steps
-void sir_batch_finish(SirBatch &sb, amb_pop **pops, const uint32_t *steps, uint32_t n);
-void sir_batch_release(SirBatch &sb, cudaStream_t s);
+// Re-derive a SIR population's band geometry for `shape` (records unchanged).
+amb_status sir_band_regeometry(amb_pop *pop, BandShape shape);
+// Fewest-bands count of an L x L grid under rows_cap (0 when unsupported).
+uint32_t sir_fewest_bands(uint32_t L, uint32_t rows_cap, uint32_t smem_cap);
 
 amb_status check_params(amb_model model, const amb_params *p, uint64_t seed);
 bool injected_create_failure();

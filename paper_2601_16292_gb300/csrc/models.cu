@@ -10,7 +10,9 @@
 //    infection / recovery pass reading the per-cell infected counts.
 #include <algorithm>
 
-#include "amb_internal.cuh"
+#include <cooperative_groups.h>
+
+#include "wealth_device.cuh"
 
 namespace amb {
 
@@ -19,29 +21,10 @@ __global__ void __launch_bounds__(256) walk_kernel(int32_t *__restrict__ x, int3
                                                    int32_t L, uint32_t k0, uint32_t k1, uint32_t t0, uint32_t k,
                                                    uint32_t *err, int64_t *__restrict__ rows)
 {
-    // per-step rows {n, 0, 0, 0}: the agent count never changes
-    if (blockIdx.x == 0)
-        for (uint32_t j = threadIdx.x; j < k; j += blockDim.x) {
-            rows[(size_t)j * 4u] = n;
-            rows[(size_t)j * 4u + 1] = 0;
-            rows[(size_t)j * 4u + 2] = 0;
-            rows[(size_t)j * 4u + 3] = 0;
-        }
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int32_t xi = x[i], yi = y[i];
-        if ((uint32_t)xi >= (uint32_t)L || (uint32_t)yi >= (uint32_t)L) {
-            atomicOr(err, ERR_RANGE);
-            continue;
-        }
-        for (uint32_t s = 0; s < k; ++s) {
-            const U4 u = philox(i, t0 + s, k0, k1);
-            const uint32_t d = u.w0 >> 29;
-            xi = ring_add(xi, dir_dx(d), L);
-            yi = ring_add(yi, dir_dy(d), L);
-        }
-        x[i] = xi;
-        y[i] = yi;
-    }
+    if (blockIdx.x == 0) walk_rows(rows, n, k);
+    const uint32_t per = (n + gridDim.x - 1u) / gridDim.x;
+    const uint32_t first = min(n, blockIdx.x * per), last = min(n, first + per);
+    walk_range(x, y, first, last, L, k0, k1, t0, k, err);
 }
 
 amb_status walk_steps(amb_pop *pop, uint32_t k)
@@ -57,86 +40,6 @@ amb_status walk_steps(amb_pop *pop, uint32_t k)
 }
 
 // ------------------------------------------------------------- wealth ------
-constexpr int kWealthNT = 1024;
-// w (4 B) + donor list (2 B) per agent in shared memory
-constexpr uint32_t kWealthSmemMaxN = 36864;
-
-__device__ __forceinline__ uint32_t lanemask_lt()
-{
-    uint32_t m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
-
-// One CTA, whole column resident in shared memory, k steps.
-__device__ __forceinline__ void wealth_cta_steps(int32_t *__restrict__ wg, uint32_t n, uint32_t k0, uint32_t k1,
-                                                 uint32_t t0, uint32_t k, int64_t *__restrict__ series)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    int32_t *w = reinterpret_cast<int32_t *>(smem_raw);
-    const uint32_t n_pad = (n + 7u) & ~7u;
-    uint16_t *donors = reinterpret_cast<uint16_t *>(w + n_pad);
-    __shared__ uint32_t s_nd;
-    __shared__ long long s_red[kWealthNT / 32];
-
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int NW = kWealthNT / 32;
-    for (uint32_t i = threadIdx.x; i < n; i += kWealthNT) w[i] = wg[i];
-    for (uint32_t s = 0; s < k; ++s) {
-        const uint32_t t = t0 + s;
-        if (threadIdx.x == 0) s_nd = 0;
-        __syncthreads();
-        uint32_t nd = 0;
-        if (n >= 2) {
-            // filtered view: donors = {w > 0} on the snapshot, compacted per warp;
-            // each agent is read and debited only by its own lane here
-            for (uint32_t base = (uint32_t)warp * 32u; base < n; base += NW * 32u) {
-                const uint32_t i = base + (uint32_t)lane;
-                const bool pred = (i < n) && (w[i] > 0);
-                const uint32_t mask = __ballot_sync(0xffffffffu, pred);
-                if (mask) {
-                    uint32_t off = 0;
-                    if (lane == 0) off = atomicAdd(&s_nd, (uint32_t)__popc(mask));
-                    off = __shfl_sync(0xffffffffu, off, 0);
-                    if (pred) {
-                        donors[off + (uint32_t)__popc(mask & lanemask_lt())] = (uint16_t)i;
-                        w[i] -= 1;
-                    }
-                }
-            }
-            __syncthreads();
-            nd = s_nd;
-            // scatter view: one unit to a uniformly chosen other agent
-            for (uint32_t j = threadIdx.x; j < nd; j += kWealthNT) {
-                const uint32_t i = donors[j];
-                const U4 u = philox(i, t, k0, k1);
-                uint32_t r = below(u.w0, n - 1u);
-                r += (r >= i) ? 1u : 0u;
-                atomicAdd(&w[r], 1);
-            }
-            __syncthreads();
-        }
-        // total wealth after the step
-        long long part = 0;
-        for (uint32_t i = threadIdx.x; i < n; i += kWealthNT) part += w[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
-        if (lane == 0) s_red[warp] = part;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            long long tot = 0;
-            for (int q = 0; q < NW; ++q) tot += s_red[q];
-            int64_t *row = series + (size_t)s * 4u;
-            row[0] = (int64_t)nd;
-            row[1] = tot;
-            row[2] = 0;
-            row[3] = 0;
-        }
-        __syncthreads();
-    }
-    for (uint32_t i = threadIdx.x; i < n; i += kWealthNT) wg[i] = w[i];
-}
-
 __global__ void __launch_bounds__(kWealthNT) wealth_smem_kernel(int32_t *__restrict__ wg, uint32_t n, uint32_t k0,
                                                                 uint32_t k1, uint32_t t0, uint32_t k,
                                                                 int64_t *__restrict__ series)
@@ -144,217 +47,23 @@ __global__ void __launch_bounds__(kWealthNT) wealth_smem_kernel(int32_t *__restr
     wealth_cta_steps(wg, n, k0, k1, t0, k, series);
 }
 
-// ------------------------------------------------------- wealth batches ---
-// Device descriptor of one wealth population in a batch.
-struct WealthJob {
-    int32_t *w;
-    int32_t *credit;  // large populations
-    int64_t *series;  // row 0 = the population's step 0
-    uint32_t n, k0, k1, t, t_end, pad;
-};
-
-// Small populations: one CTA per job runs all its remaining steps.
-__global__ void __launch_bounds__(kWealthNT) wealth_batch_small_kernel(WealthJob *__restrict__ jobs,
-                                                                       const uint32_t *__restrict__ list)
-{
-    WealthJob &j = jobs[list[blockIdx.x]];
-    if (j.t < j.t_end) wealth_cta_steps(j.w, j.n, j.k0, j.k1, j.t, j.t_end - j.t, j.series + (size_t)j.t * 4u);
-}
-
-constexpr uint32_t kWealthChunk = 2048;  // agents per block in the batched grid-wide kernels
-
-__device__ __forceinline__ uint32_t chunk_job(const uint32_t *prefix, uint32_t n_jobs, uint32_t g)
-{
-    uint32_t lo = 0, hi = n_jobs - 1;  // last job whose first chunk <= g
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi + 1) >> 1;
-        if (prefix[mid] <= g)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
-
-// Large populations, one step: donors credit their recipients (phase 1).
-__global__ void __launch_bounds__(256) wealth_batch_donate_kernel(const WealthJob *__restrict__ jobs,
-                                                                  const uint32_t *__restrict__ list,
-                                                                  const uint32_t *__restrict__ prefix, uint32_t n_jobs)
-{
-    __shared__ uint32_t s_job;
-    if (threadIdx.x == 0) s_job = chunk_job(prefix, n_jobs, blockIdx.x);
-    __syncthreads();
-    const WealthJob &j = jobs[list[s_job]];
-    if (j.t >= j.t_end) return;
-    const uint32_t first = (blockIdx.x - prefix[s_job]) * kWealthChunk;
-    const uint32_t last = min(first + kWealthChunk, j.n);
-    uint32_t local = 0;
-    for (uint32_t i = first + threadIdx.x; i < last; i += blockDim.x) {
-        if (j.w[i] > 0) {
-            const U4 u = philox(i, j.t, j.k0, j.k1);
-            uint32_t r = below(u.w0, j.n - 1u);
-            r += (r >= i) ? 1u : 0u;
-            atomicAdd(&j.credit[r], 1);
-            ++local;
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) local += __shfl_down_sync(0xffffffffu, local, o);
-    if ((threadIdx.x & 31) == 0 && local)
-        atomicAdd(reinterpret_cast<unsigned long long *>(&j.series[(size_t)j.t * 4u]), (unsigned long long)local);
-}
-
-// Large populations, one step: w' = w - [w > 0] + credit (phase 2).
-__global__ void __launch_bounds__(256) wealth_batch_apply_kernel(const WealthJob *__restrict__ jobs,
-                                                                 const uint32_t *__restrict__ list,
-                                                                 const uint32_t *__restrict__ prefix, uint32_t n_jobs)
-{
-    __shared__ uint32_t s_job;
-    if (threadIdx.x == 0) s_job = chunk_job(prefix, n_jobs, blockIdx.x);
-    __syncthreads();
-    const WealthJob &j = jobs[list[s_job]];
-    if (j.t >= j.t_end) return;
-    const uint32_t first = (blockIdx.x - prefix[s_job]) * kWealthChunk;
-    const uint32_t last = min(first + kWealthChunk, j.n);
-    long long part = 0;
-    for (uint32_t i = first + threadIdx.x; i < last; i += blockDim.x) {
-        const int32_t wi = j.w[i];
-        const int32_t nw = (int32_t)((uint32_t)wi - (wi > 0 ? 1u : 0u) + (uint32_t)j.credit[i]);
-        j.w[i] = nw;
-        j.credit[i] = 0;
-        part += nw;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
-    if ((threadIdx.x & 31) == 0 && part)
-        atomicAdd(reinterpret_cast<unsigned long long *>(&j.series[(size_t)j.t * 4u + 1u]), (unsigned long long)part);
-}
-
-__global__ void wealth_batch_advance_kernel(WealthJob *__restrict__ jobs, const uint32_t *__restrict__ list,
-                                            uint32_t n_jobs)
-{
-    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n_jobs; q += gridDim.x * blockDim.x) {
-        WealthJob &j = jobs[list[q]];
-        if (j.t < j.t_end) j.t += 1u;
-    }
-}
-
-// Host side: a set of wealth populations advanced together.
-amb_status wealth_batch_build(WealthBatch &wb, amb_pop **pops, const uint32_t *steps, uint32_t n, cudaStream_t s)
-{
-    std::vector<WealthJob> jobs(n);
-    std::vector<uint32_t> small, large, prefix(1, 0u);
-    size_t smem = 16;
-    for (uint32_t q = 0; q < n; ++q) {
-        amb_pop *p = pops[q];
-        WealthJob &j = jobs[q];
-        j.w = p->w;
-        j.credit = p->credit;
-        j.series = p->series;
-        j.n = p->p.n;
-        j.k0 = p->key0;
-        j.k1 = p->key1;
-        j.t = (uint32_t)p->t;
-        j.t_end = (uint32_t)(p->t + steps[q]);
-        j.pad = 0;
-        if (p->p.n == 0 || steps[q] == 0) continue;
-        if (wealth_uses_smem(p->p.n)) {
-            small.push_back(q);
-            smem = std::max(smem, (size_t)((p->p.n + 7u) & ~7u) * 4u + (size_t)p->p.n * 2u + 16u);
-        } else {
-            large.push_back(q);
-            prefix.push_back(prefix.back() + (p->p.n + kWealthChunk - 1u) / kWealthChunk);
-        }
-    }
-    wb.n_jobs = n;
-    wb.n_small = (uint32_t)small.size();
-    wb.n_large = (uint32_t)large.size();
-    wb.large_chunks = prefix.back();
-    wb.smem = smem;
-    AMB_TRY(dalloc(reinterpret_cast<unsigned char **>(&wb.d_jobs), (size_t)n * sizeof(WealthJob), s));
-    AMB_TRY(dalloc(&wb.d_small, small.size(), s));
-    AMB_TRY(dalloc(&wb.d_large, large.size(), s));
-    AMB_TRY(dalloc(&wb.d_prefix, prefix.size(), s));
-    AMB_TRY_CUDA(cudaMemcpyAsync(wb.d_jobs, jobs.data(), (size_t)n * sizeof(WealthJob), cudaMemcpyHostToDevice, s));
-    if (!small.empty())
-        AMB_TRY_CUDA(cudaMemcpyAsync(wb.d_small, small.data(), small.size() * 4u, cudaMemcpyHostToDevice, s));
-    if (!large.empty())
-        AMB_TRY_CUDA(cudaMemcpyAsync(wb.d_large, large.data(), large.size() * 4u, cudaMemcpyHostToDevice, s));
-    AMB_TRY_CUDA(cudaMemcpyAsync(wb.d_prefix, prefix.data(), prefix.size() * 4u, cudaMemcpyHostToDevice, s));
-    AMB_TRY_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
-    return AMB_OK;
-}
-
-// Every small job, all of its steps (one launch).
-amb_status wealth_batch_small(WealthBatch &wb, cudaStream_t s, uint64_t *launches)
-{
-    if (wb.n_small == 0) return AMB_OK;
-    AMB_TRY_CUDA(cudaFuncSetAttribute(wealth_batch_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)wb.smem));
-    wealth_batch_small_kernel<<<wb.n_small, kWealthNT, wb.smem, s>>>(static_cast<WealthJob *>(wb.d_jobs), wb.d_small);
-    AMB_TRY_CUDA(cudaGetLastError());
-    *launches += 1;
-    return AMB_OK;
-}
-
-// One step of every large job (three launches).
-amb_status wealth_batch_large_step(WealthBatch &wb, cudaStream_t s, uint64_t *launches)
-{
-    if (wb.n_large == 0) return AMB_OK;
-    WealthJob *jobs = static_cast<WealthJob *>(wb.d_jobs);
-    wealth_batch_donate_kernel<<<wb.large_chunks, 256, 0, s>>>(jobs, wb.d_large, wb.d_prefix, wb.n_large);
-    wealth_batch_apply_kernel<<<wb.large_chunks, 256, 0, s>>>(jobs, wb.d_large, wb.d_prefix, wb.n_large);
-    wealth_batch_advance_kernel<<<grid_for(wb.n_large, 128), 128, 0, s>>>(jobs, wb.d_large, wb.n_large);
-    AMB_TRY_CUDA(cudaGetLastError());
-    *launches += 3;
-    return AMB_OK;
-}
-
-void wealth_batch_release(WealthBatch &wb, cudaStream_t s)
-{
-    void *j = wb.d_jobs;
-    dfree(j, s);
-    wb.d_jobs = nullptr;
-    dfree(wb.d_small, s);
-    dfree(wb.d_large, s);
-    dfree(wb.d_prefix, s);
-}
-
 // Grid-wide path, phase 1: donors on the snapshot credit their recipient.
 __global__ void __launch_bounds__(256) wealth_donate_kernel(const int32_t *__restrict__ w, int32_t *__restrict__ credit,
                                                             uint32_t n, uint32_t k0, uint32_t k1, uint32_t t,
                                                             int64_t *__restrict__ row)
 {
-    uint32_t local = 0;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        if (w[i] > 0) {
-            const U4 u = philox(i, t, k0, k1);
-            uint32_t r = below(u.w0, n - 1u);
-            r += (r >= i) ? 1u : 0u;
-            atomicAdd(&credit[r], 1);
-            ++local;
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) local += __shfl_down_sync(0xffffffffu, local, o);
-    if ((threadIdx.x & 31) == 0 && local) atomicAdd(reinterpret_cast<unsigned long long *>(&row[0]), (unsigned long long)local);
+    const uint32_t per = (n + gridDim.x - 1u) / gridDim.x;
+    const uint32_t first = min(n, blockIdx.x * per);
+    wealth_donate_range(w, credit, n, k0, k1, t, first, min(n, first + per), row);
 }
 
 // Grid-wide path, phase 2: w' = w - [w > 0] + credit; credit cleared.
 __global__ void __launch_bounds__(256) wealth_apply_kernel(int32_t *__restrict__ w, int32_t *__restrict__ credit,
                                                            uint32_t n, int64_t *__restrict__ row)
 {
-    long long part = 0;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int32_t wi = w[i];
-        const int32_t nw = (int32_t)((uint32_t)wi - (wi > 0 ? 1u : 0u) + (uint32_t)credit[i]);
-        w[i] = nw;
-        credit[i] = 0;
-        part += nw;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
-    if ((threadIdx.x & 31) == 0 && part) atomicAdd(reinterpret_cast<unsigned long long *>(&row[1]), (unsigned long long)part);
+    const uint32_t per = (n + gridDim.x - 1u) / gridDim.x;
+    const uint32_t first = min(n, blockIdx.x * per);
+    wealth_apply_range(w, credit, first, min(n, first + per), row);
 }
 
 __global__ void wealth_total_kernel(const int32_t *__restrict__ w, uint32_t n, int64_t *__restrict__ row)
@@ -368,6 +77,141 @@ __global__ void wealth_total_kernel(const int32_t *__restrict__ w, uint32_t n, i
 
 bool wealth_uses_smem(uint32_t n) { return n <= kWealthSmemMaxN; }
 
+// ------------------------------------------------- wealth, one cluster ---
+// All k steps of a column of n agents (kClusterMinN <= n <= kWealthSmemMaxN)
+// on one thread-block cluster: CTA q of the cluster keeps agents
+// [q per, (q+1) per) in its shared memory, with two credit arrays used in
+// alternate steps.  Step t, every CTA, its own agents only: fold in the
+// credits of step t-1, take the donors on that snapshot, debit them, and add
+// one unit to each recipient's credit word of step t in the owning CTA's
+// shared memory (distributed shared memory atomics); then one cluster
+// barrier.  Credits of step t land in the other array than those being
+// folded, and a CTA can only start step t+1 after every CTA has passed step
+// t's barrier, i.e. finished folding step t-1's credits, so one barrier per
+// step suffices.  The total after step t is summed while step t+1 folds (a
+// final fold after the last step).
+constexpr int kClusterNT = 256;
+constexpr uint32_t kClusterMinN = 4096;
+
+__global__ void __launch_bounds__(kClusterNT) wealth_cluster_kernel(int32_t *__restrict__ wg, uint32_t n, uint32_t per,
+                                                                    uint32_t inv_per, uint32_t k0, uint32_t k1,
+                                                                    uint32_t t0, uint32_t k, int64_t *__restrict__ rows)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ __align__(16) int32_t cl_smem[];
+    __shared__ long long s_red[kClusterNT / 32];
+    __shared__ uint32_t s_donors[kClusterNT / 32];
+    int32_t *w = cl_smem;            // own agents
+    int32_t *cr0 = cl_smem + per;    // credits of even steps
+    int32_t *cr1 = cl_smem + 2 * per;  // credits of odd steps
+    const uint32_t q = cluster.block_rank();
+    const uint32_t lo = q * per, hi = min(n, lo + per), mine = hi > lo ? hi - lo : 0u;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    for (uint32_t i = tid; i < per; i += kClusterNT) {
+        w[i] = i < mine ? wg[lo + i] : 0;
+        cr0[i] = 0;
+        cr1[i] = 0;
+    }
+    cluster.sync();
+    for (uint32_t s = 0; s <= k; ++s) {  // s = k: the final fold
+        const uint32_t t = t0 + s;
+        int32_t *fold = ((t & 1u) ? cr0 : cr1);   // credits of step t-1
+        int32_t *give = ((t & 1u) ? cr1 : cr0);   // credits of step t
+        long long total = 0;
+        uint32_t donors = 0;
+        for (uint32_t i = tid; i < mine; i += kClusterNT) {
+            int32_t wi = (int32_t)((uint32_t)w[i] + (uint32_t)fold[i]);
+            fold[i] = 0;
+            total += wi;
+            if (s < k && n >= 2 && wi > 0) {
+                wi -= 1;
+                ++donors;
+                const uint32_t id = lo + i;
+                const U4 u = philox(id, t, k0, k1);
+                uint32_t r = below(u.w0, n - 1u);
+                r += (r >= id) ? 1u : 0u;
+                const uint32_t owner = __umulhi(r, inv_per);  // r / per, exact for these sizes
+                int32_t *dst = cluster.map_shared_rank(give, owner);
+                atomicAdd(dst + (r - owner * per), 1);
+            }
+            w[i] = wi;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            total += __shfl_down_sync(0xffffffffu, total, o);
+            donors += __shfl_down_sync(0xffffffffu, donors, o);
+        }
+        if (lane == 0) {
+            s_red[warp] = total;
+            s_donors[warp] = donors;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            long long tt = 0;
+            uint32_t dd = 0;
+            for (int j = 0; j < kClusterNT / 32; ++j) {
+                tt += s_red[j];
+                dd += s_donors[j];
+            }
+            // the total after step t-1 (the folded snapshot), the donors of step t
+            if (s > 0 && tt) atomicAdd(reinterpret_cast<unsigned long long *>(&rows[(size_t)(s - 1) * 4u + 1u]),
+                                       (unsigned long long)tt);
+            if (s < k && dd) atomicAdd(reinterpret_cast<unsigned long long *>(&rows[(size_t)s * 4u]),
+                                       (unsigned long long)dd);
+        }
+        if (s < k) cluster.sync();
+    }
+    for (uint32_t i = tid; i < mine; i += kClusterNT) wg[lo + i] = w[i];
+}
+
+// One launch of wealth_cluster_kernel: 16 CTAs per cluster where the device
+// allows it, else 8.
+static amb_status wealth_cluster_steps(amb_pop *pop, uint32_t k, int64_t *rows)
+{
+    const uint32_t n = pop->p.n;
+    static int cluster_size = 0;  // chosen on the first launch
+    for (int c : {16, 8}) {
+        if (cluster_size && c != cluster_size) continue;
+        const uint32_t per = (n + (uint32_t)c - 1u) / (uint32_t)c;
+        const uint32_t inv_per = (uint32_t)((0x100000000ull + per - 1u) / per);  // ceil(2^32 / per)
+        const size_t smem = (size_t)per * 3u * sizeof(int32_t);
+        if (cudaFuncSetAttribute(wealth_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, c > 8) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(wealth_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess) {
+            (void)cudaGetLastError();
+            continue;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)c);
+        cfg.blockDim = dim3(kClusterNT);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = pop->stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)c;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, wealth_cluster_kernel, &cfg) != cudaSuccess || clusters < 1) {
+            (void)cudaGetLastError();
+            continue;
+        }
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, wealth_cluster_kernel, pop->w, n, per, inv_per, pop->key0,
+                                                 pop->key1, (uint32_t)pop->t, k, rows);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            continue;
+        }
+        cluster_size = c;
+        return AMB_OK;
+    }
+    return fail(AMB_ECUDA, "no thread-block cluster configuration could be launched");
+}
+
 amb_status wealth_steps(amb_pop *pop, uint32_t k)
 {
     const uint32_t n = pop->p.n;
@@ -375,6 +219,11 @@ amb_status wealth_steps(amb_pop *pop, uint32_t k)
     if (k == 0) return AMB_OK;
     AMB_TRY_CUDA(cudaMemsetAsync(rows, 0, (size_t)k * 4u * sizeof(int64_t), pop->stream));
     if (n == 0) return AMB_OK;
+    if (n >= kClusterMinN && wealth_uses_smem(n)) {
+        AMB_TRY(wealth_cluster_steps(pop, k, rows));
+        pop->launches += 1;
+        return AMB_OK;
+    }
     if (wealth_uses_smem(n)) {
         const size_t smem = (size_t)((n + 7u) & ~7u) * 4u + (size_t)n * 2u + 16u;
         AMB_TRY_CUDA(cudaFuncSetAttribute(wealth_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -34,6 +34,7 @@ namespace {
 
 constexpr size_t kIterationReserve = size_t(512) << 20;  // launch tables, wide band counters
 constexpr size_t kPoolSlack = size_t(64) << 10;          // per population: pool rounding, small buffers
+constexpr uint32_t kMinChunk = 8;                        // fewest steps of an iteration (unless chunk_steps is lower)
 
 size_t series_bytes(uint32_t steps)
 {
@@ -168,6 +169,7 @@ void worker_loop(amb_server *S)
     shape.rows_cap = S->cfg.band_rows_cap ? std::min<uint32_t>(S->cfg.band_rows_cap, 32u) : 16u;
     shape.spread = S->cfg.spread_bands > 0;
     shape.adaptive = S->cfg.spread_bands == 0;
+    double step_us = 0.0;  // device time per step of the last iteration
     for (;;) {
         std::vector<ServerJob *> admit;
         {
@@ -204,18 +206,28 @@ void worker_loop(amb_server *S)
         }
         if (S->active.empty()) continue;
 
-        // one iteration: every active job advances by up to `chunk` steps
+        // one iteration: every active job advances by up to `k_it` steps: at
+        // most `chunk`, no further than the step where the first active job
+        // finishes, and (with a time target) no more steps than the previous
+        // iteration's device time per step says fit in the target; at least
+        // min(kMinChunk, chunk)
         AMB_TRACE("amb_server_iteration");
         const double t0 = S->now();
         std::vector<amb_pop *> pops;
         std::vector<uint32_t> ks;
+        uint32_t k_it = chunk;
+        for (ServerJob *j : S->active) k_it = std::min<uint32_t>(k_it, j->job.steps - j->done_steps);
+        if (S->cfg.iteration_us && step_us > 0.0)
+            k_it = std::min<uint32_t>(k_it, (uint32_t)std::max(1.0, (double)S->cfg.iteration_us / step_us));
+        k_it = std::max<uint32_t>(k_it, std::min<uint32_t>(kMinChunk, chunk));
         for (ServerJob *j : S->active) {
             pops.push_back(j->pop);
-            ks.push_back(std::min<uint32_t>(chunk, j->job.steps - j->done_steps));
+            ks.push_back(std::min<uint32_t>(k_it, j->job.steps - j->done_steps));
         }
         uint64_t launches = 0;
         float ms = 0.f;
         amb_status st = advance(pops, ks, shape, S->stream, false, &launches, &ms);
+        if (st == AMB_OK && ms > 0.f) step_us = 1000.0 * (double)ms / (double)k_it;
         std::vector<uint32_t> words;
         if (st == AMB_OK) st = read_errors(pops, S->stream, words);
         std::vector<ServerJob *> still;

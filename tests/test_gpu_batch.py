@@ -85,3 +85,48 @@ def test_batch_runs_once():
     with pytest.raises(amb.AmbError):
         b.run()
     b.close()
+
+
+def test_batch_is_one_persistent_launch(expected):
+    # the whole run (every job, every step) is one kernel launch
+    stream = torch.cuda.Stream()
+    b = amb.Batch(JOBS, stream=stream)
+    b.run()
+    assert b.info()["launches"] == 1
+    _check_batch(b, expected)
+    b.close()
+
+
+def test_many_uneven_jobs_equal_lone_runs(_cuda):
+    # 60 jobs of every kind with uneven sizes and step counts share one
+    # persistent launch (steps of different jobs interleave in its queue);
+    # each equals the same job stepped alone
+    rng = np.random.default_rng(17)
+    jobs = []
+    for i in range(60):
+        kind = ("sir", "wealth", "walk")[i % 3]
+        n = int(rng.integers(0, 90_000)) if i % 7 else int(rng.integers(0, 40))
+        steps = int(rng.integers(0, 40))
+        if kind == "sir":
+            L = max(1, int(rng.integers(1, 400)))
+            jobs.append(dict(model="sir", n=n, L=L, beta=float(rng.uniform(0, 0.4)), gamma=float(rng.uniform(0, 0.2)),
+                             n0=min(n, int(rng.integers(0, 50))), seed=100 + i, rep=i, steps=steps))
+        elif kind == "wealth":
+            jobs.append(dict(model="wealth", n=n, seed=100 + i, rep=i, steps=steps, w_init=int(rng.integers(0, 3))))
+        else:
+            jobs.append(dict(model="walk", n=n, L=max(1, int(rng.integers(1, 300))), seed=100 + i, rep=i, steps=steps))
+    stream = torch.cuda.Stream()
+    b = amb.Batch(jobs, stream=stream)
+    b.run()
+    assert b.info()["launches"] <= 1
+    for i, j in enumerate(jobs):
+        kw = {k: v for k, v in j.items() if k not in ("model", "steps")}
+        alone = amb.Population(j["model"], stream=stream, **kw).step(j["steps"])
+        v = b.population(i)
+        assert v.t == j["steps"]
+        assert np.array_equal(v.counts(), alone.counts()), (i, j)
+        cols = ("wealth",) if j["model"] == "wealth" else (("x", "y", "state") if j["model"] == "sir" else ("x", "y"))
+        for c in cols:
+            assert torch.equal(v.column(c), alone.column(c)), (i, j, c)
+        alone.close()
+    b.close()
