@@ -822,7 +822,7 @@ def main():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="amb", choices=["amb", "reference"])
-    ap.add_argument("--only", default="all", choices=["all", "sir", "sweep", "serve", "views", "paper"],
+    ap.add_argument("--only", default="all", choices=["all", "sir", "sweep", "serve", "views", "paper", "models"],
                     help="sir: time the SIR step alone (no extras; for profiling); sweep / serve: that part alone")
     ap.add_argument("--serve-jobs", type=int, default=5000)
     ap.add_argument("--serve-chunk", type=int, default=32)
@@ -834,6 +834,14 @@ def main():
         from paper_2601_16292_gb300 import amb
         torch.cuda.set_device(0)
         print(json.dumps(sweep_bench(amb, torch, torch.cuda.Stream(), 0, 1)))
+        return
+    if args.impl == "amb" and args.only == "models":
+        import torch
+        from paper_2601_16292_gb300 import amb
+        torch.cuda.set_device(0)
+        st = torch.cuda.Stream()
+        print(json.dumps({"wealth_10k_100steps": time_model_block(amb, torch, "wealth", WEALTH_CFG, st, 0),
+                          "walk_1M_L1000_200steps": time_model_block(amb, torch, "walk", WALK_CFG, st, 0)}))
         return
     if args.impl == "amb" and args.only == "paper":
         import torch

@@ -285,11 +285,13 @@ amb_status amb_cell_index(const int32_t *x, const int32_t *y, uint32_t n, uint32
 /* ------------------------------------------------------------ batches ----
  * Many independent jobs advanced together on one GPU (the paper's Experiment
  * with replications and ParallelRunner, Sec. 4.2, re-cast for one device):
- * every SIR step of every job is one shared launch over all their bands; small
- * wealth jobs run in one launch, one CTA each; large wealth jobs take three
- * shared launches per step; walk jobs one launch each.  The run is captured
- * into one CUDA graph and launched once (use_graph = 1, the default).
- * Results are bit-identical to stepping each job alone with amb_step.
+ * at most three persistent kernel launches (the SIR jobs; the wealth jobs
+ * whose column fits one CTA's shared memory; the other wealth and the walk
+ * jobs), each draining a device work queue of all of its jobs' steps (one
+ * CTA per SM; a job's steps follow one another, different jobs' steps
+ * overlap).  The run is captured into one CUDA graph and launched once
+ * (use_graph = 1, the default).  Results are bit-identical to stepping each
+ * job alone with amb_step.
  */
 typedef struct {
     amb_model model;

@@ -1,16 +1,18 @@
 // batch.cu -- many independent simulation jobs advanced together (the
-// paper's Experiment / ParallelRunner, Sec. 4.2, re-cast for one GPU) by ONE
-// persistent kernel launch: one CTA per SM takes work units from a device
-// queue until every job has taken all of its steps.
+// paper's Experiment / ParallelRunner, Sec. 4.2, re-cast for one GPU) by
+// persistent kernel launches: one CTA per SM takes work units from a device
+// queue until every job has taken all of its steps.  The SIR jobs, the small
+// wealth jobs and the other jobs take one launch each, one after the other,
+// because a launch takes the largest shared memory its jobs need.
 //
 // Queue.  An entry is a piece of work made of `units` independent units:
 //   * one step of a SIR job (units = its bands, taken in band order, each
 //     band's output slot found by decoupled look-back inside the step);
 //   * phase 1 or phase 2 of one step of a large wealth job (units = chunks of
-//     8,192 agents: donors credit their recipients; w' = w - [w > 0] + credit);
+//     32,768 agents: donors credit their recipients; w' = w - [w > 0] + credit);
 //   * all steps of a small wealth job (one unit: the column in one CTA's
 //     shared memory);
-//   * all steps of a walk job (units = chunks of 8,192 agents, steps fused).
+//   * all steps of a walk job (units = chunks of 32,768 agents, steps fused).
 // A CTA claims the next unit of the head entry with one atomic; when the
 // entry's units are all claimed the head moves on.  The CTA that completes
 // the last unit of an entry publishes the job's next entry at the tail (the
@@ -36,7 +38,7 @@
 namespace amb {
 
 enum : uint32_t { kKindSir = 0, kKindWealthSmall = 1, kKindDonate = 2, kKindApply = 3, kKindWalk = 4 };
-constexpr uint32_t kUnitAgents = 8192;              // agents per unit of wealth phases and walks
+constexpr uint32_t kUnitAgents = 32768;             // agents per unit of wealth phases and walks
 constexpr uint64_t kIdleLimitNs = 4ull * kSpinLimitNs;  // an idle CTA gives up after waiting this long
 
 struct SirJob {
@@ -205,16 +207,16 @@ __global__ void __launch_bounds__(kBandNT, 1) persist_kernel(const PersistArgs p
     if (tid < 4) sh.cnt[tid] = 0ull;
     Tally tl = {0u, 0u, 0u, 0u};
     uint32_t *wide_slice = pa.wide ? pa.wide + (size_t)blockIdx.x * pa.wide_words : nullptr;
+    if (tid == 0) {
+        QEntry e;
+        uint32_t h = 0, u = 0;
+        s_go = claim_unit(pa, h, u, e, false) ? 1u : 0u;
+        s_h = h;
+        s_u = u;
+        s_e = e;
+    }
+    __syncthreads();
     for (;;) {
-        if (tid == 0) {
-            QEntry e = s_e;
-            uint32_t h = s_h, u = 0;
-            s_go = claim_unit(pa, h, u, e, s_go != 0u) ? 1u : 0u;
-            s_h = h;
-            s_u = u;
-            s_e = e;
-        }
-        __syncthreads();
         if (!s_go) break;
         const QEntry e = s_e;
         const uint32_t u = s_u;
@@ -262,15 +264,30 @@ __global__ void __launch_bounds__(kBandNT, 1) persist_kernel(const PersistArgs p
                     wealth_apply_range(w.w, w.credit, first, last, row);
             }
         }
-        // the unit's writes are visible GPU-wide before it is counted done
+        // the unit's writes are visible GPU-wide before it is counted done;
+        // the next unit of the same entry is claimed by an atomic issued
+        // together with the count (a claim that has to wait for an entry to
+        // be published comes only after the count, which may publish it)
         __threadfence();
         __syncthreads();
         if (tid == 0) {
+            const uint32_t u_next = atomicAdd(&pa.claimed[s_h], 1u);
             if (atomicAdd(&pa.done[s_h], 1u) + 1u == e.units) {
                 __threadfence();
                 entry_done(pa, e);
             }
+            if (u_next < e.units) {
+                s_u = u_next;
+            } else {
+                QEntry ne = e;
+                uint32_t h = s_h, u = 0;
+                s_go = claim_unit(pa, h, u, ne, false) ? 1u : 0u;
+                s_h = h;
+                s_u = u;
+                s_e = ne;
+            }
         }
+        __syncthreads();
     }
 }
 
@@ -480,7 +497,16 @@ static amb_status persist_build(PersistBatch &pb, const std::vector<amb_pop *> &
     pa.n_entries = (uint32_t)n_entries;
     pa.wide = pb.wide;
     pa.wide_words = (uint32_t)wide_words;
-    AMB_TRY_CUDA(cudaFuncSetAttribute(persist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pb.smem));
+    // the kernel may take as much dynamic shared memory as the device allows
+    // (set once, to the largest value: every launch asks for its own size)
+    static bool attr_set = false;
+    if (!attr_set) {
+        AMB_TRY_CUDA(cudaFuncSetAttribute(persist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          optin - (int)static_smem));
+        attr_set = true;
+    }
+    if (pb.smem > (size_t)(optin - (int)static_smem))
+        return fail(AMB_EINVAL, "a batch needs %zu bytes of shared memory per CTA", pb.smem);
     return AMB_OK;
 }
 
@@ -510,8 +536,8 @@ static void persist_finish(PersistBatch &pb)
 }
 
 // Advance every population by its own number of steps (ks[i] for pops[i]) in
-// one persistent launch (captured as a one-node CUDA graph with graph).
-// *ms: device time of the launch (events on s).  Returns after the work is
+// at most three persistent launches (captured as one CUDA graph with graph).
+// *ms: device time of the launches (events on s).  Returns after the work is
 // done.
 amb_status advance(const std::vector<amb_pop *> &pops, const std::vector<uint32_t> &ks, BandShape shape,
                    cudaStream_t s, bool graph, uint64_t *launches_out, float *ms_out)
@@ -524,22 +550,43 @@ amb_status advance(const std::vector<amb_pop *> &pops, const std::vector<uint32_
         AMB_TRY(ensure_series(p, p->t + k));
         if (k) AMB_TRY_CUDA(cudaMemsetAsync(p->series + (size_t)p->t * 4u, 0, (size_t)k * 4u * sizeof(int64_t), s));
     }
-    PersistBatch pb;
-    amb_status r = persist_build(pb, pops, ks, shape, s, nullptr);
-    cudaGraph_t g = nullptr;
+    // up to three persistent launches, one after the other, by the shared
+    // memory their CTAs need: the SIR jobs (band counters), the small wealth
+    // jobs (their columns), the large wealth and walk jobs (none).  A launch
+    // takes the largest shared memory of its jobs, and the L1 left beside it
+    // then limits the memory requests in flight of the large wealth jobs'
+    // phases: small and large wealth jobs in one launch took 290 ms on the
+    // 1,024-job sweep, apart 159 ms.
+    constexpr int kGroups = 3;
+    std::vector<amb_pop *> gp[kGroups];
+    std::vector<uint32_t> gk[kGroups];
+    for (size_t i = 0; i < pops.size(); ++i) {
+        const amb_pop *p = pops[i];
+        const int g = p->model == AMB_SIR ? 0 : (p->model == AMB_WEALTH && wealth_uses_smem(p->p.n) ? 1 : 2);
+        gp[g].push_back(pops[i]);
+        gk[g].push_back(ks[i]);
+    }
+    PersistBatch pb[kGroups];
+    amb_status r = AMB_OK;
+    for (int g = 0; g < kGroups && r == AMB_OK; ++g) r = persist_build(pb[g], gp[g], gk[g], shape, s, nullptr);
+    cudaGraph_t gr = nullptr;
     cudaGraphExec_t ge = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     uint64_t launches = 0;
+    auto issue = [&]() -> amb_status {
+        for (int g = 0; g < kGroups; ++g) AMB_TRY(persist_launch(pb[g], s, &launches));
+        return AMB_OK;
+    };
     if (r == AMB_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         r = fail(AMB_ECUDA, "event creation failed");
     if (r == AMB_OK && graph) {
         if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
             r = fail(AMB_ECUDA, "stream capture failed to begin (is the stream the legacy default stream?)");
         } else {
-            r = persist_launch(pb, s, &launches);
-            const cudaError_t ec = cudaStreamEndCapture(s, &g);
+            r = issue();
+            const cudaError_t ec = cudaStreamEndCapture(s, &gr);
             if (r == AMB_OK && ec != cudaSuccess) r = fail(AMB_ECUDA, "capture: %s", cudaGetErrorString(ec));
-            if (r == AMB_OK && cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) r = fail(AMB_ECUDA, "graph instantiate failed");
+            if (r == AMB_OK && cudaGraphInstantiate(&ge, gr, 0) != cudaSuccess) r = fail(AMB_ECUDA, "graph instantiate failed");
         }
         if (r == AMB_OK) {
             cudaEventRecord(e0, s);
@@ -548,21 +595,22 @@ amb_status advance(const std::vector<amb_pop *> &pops, const std::vector<uint32_
         }
     } else if (r == AMB_OK) {
         cudaEventRecord(e0, s);
-        r = persist_launch(pb, s, &launches);
+        r = issue();
         cudaEventRecord(e1, s);
     }
-    uint32_t ctl[4] = {0u, 0u, 0u, 0u};
     if (r == AMB_OK) {
         const cudaError_t es = cudaEventSynchronize(e1);
         if (es != cudaSuccess) r = fail(AMB_ECUDA, "batched steps: %s", cudaGetErrorString(es));
         float ms = 0.f;
         if (r == AMB_OK) cudaEventElapsedTime(&ms, e0, e1);
         if (ms_out) *ms_out = ms;
-        if (r == AMB_OK && pb.d_ctl &&
-            cudaMemcpy(ctl, pb.d_ctl, sizeof(ctl), cudaMemcpyDeviceToHost) != cudaSuccess)
-            r = fail(AMB_ECUDA, "reading the run's status failed");
+        uint32_t ctl[kGroups][4] = {};
+        for (int g = 0; g < kGroups; ++g)
+            if (r == AMB_OK && pb[g].d_ctl &&
+                cudaMemcpy(ctl[g], pb[g].d_ctl, sizeof(ctl[g]), cudaMemcpyDeviceToHost) != cudaSuccess)
+                r = fail(AMB_ECUDA, "reading the run's status failed");
         // the populations moved on (even if the run reports a problem)
-        persist_finish(pb);
+        for (int g = 0; g < kGroups; ++g) persist_finish(pb[g]);
         for (size_t i = 0; i < pops.size(); ++i) {
             amb_pop *p = pops[i];
             p->t += ks[i];
@@ -570,18 +618,21 @@ amb_status advance(const std::vector<amb_pop *> &pops, const std::vector<uint32_
             if (p->model == AMB_WALK) p->index_valid = false;
         }
         if (launches_out) *launches_out += launches;
-        if (r == AMB_OK && (ctl[2] & ERR_TIMEOUT))
-            r = fail(AMB_ETIMEOUT, "the batched launch stopped: a wait for queued work ran out");
-        if (r == AMB_OK && ctl[2])
-            r = fail(AMB_ECUDA, "the batched launch's work queue overflowed (0x%x)", ctl[2]);
-        if (r == AMB_OK && pb.args.n_entries && ctl[0] < pb.args.n_entries)
-            r = fail(AMB_ETIMEOUT, "the batched launch ended with %u of %u entries taken", ctl[0], pb.args.n_entries);
+        for (int g = 0; g < kGroups && r == AMB_OK; ++g) {
+            if (ctl[g][2] & ERR_TIMEOUT)
+                r = fail(AMB_ETIMEOUT, "the batched launch stopped: a wait for queued work ran out");
+            else if (ctl[g][2])
+                r = fail(AMB_ECUDA, "the batched launch's work queue overflowed (0x%x)", ctl[g][2]);
+            else if (pb[g].args.n_entries && ctl[g][0] < pb[g].args.n_entries)
+                r = fail(AMB_ETIMEOUT, "the batched launch ended with %u of %u entries taken", ctl[g][0],
+                         pb[g].args.n_entries);
+        }
     }
     if (ge) cudaGraphExecDestroy(ge);
-    if (g) cudaGraphDestroy(g);
+    if (gr) cudaGraphDestroy(gr);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    pb.release(s);
+    for (int g = 0; g < kGroups; ++g) pb[g].release(s);
     cudaStreamSynchronize(s);
     return r;
 }

@@ -84,7 +84,7 @@ def test_wealth_ten_thousand_agents_hundred_steps():
     g.close()
 
 
-@pytest.mark.parametrize("n", [0, 1, 2, 3, 33, 1000, 36864, 36865, 50_000])
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 33, 1000, 4095, 4096, 4097, 20_001, 36864, 36865, 50_000])
 def test_wealth_sizes(n):
     g, o = run_pair("wealth", n, [1, 7, 12], seed=5, rep=3, w_init=2)
     if n:
@@ -96,7 +96,7 @@ def test_wealth_sizes(n):
     g.close()
 
 
-@pytest.mark.parametrize("n", [777, 60_000])
+@pytest.mark.parametrize("n", [777, 20_000, 60_000])
 def test_wealth_written_column(n):
     rng = np.random.default_rng(11)
     w0 = rng.integers(0, 6, n).astype(np.int32)
@@ -390,3 +390,21 @@ def test_stateless_cell_index_reports_out_of_range():
         amb.amb_cell_index(x, y, L, start, ids)
     assert e.value.status == amb.AMB_EINVAL
     assert int(start[-1]) == 2
+
+
+@pytest.mark.parametrize("n", [5_000, 30_000])
+def test_wealth_wraps_like_the_oracle(n):
+    # wealth arithmetic wraps modulo 2^32 on both sides (agents at the int32
+    # maximum that receive a unit turn negative and stop donating)
+    rng = np.random.default_rng(23)
+    w0 = rng.integers(0, 4, n).astype(np.int32)
+    w0[rng.choice(n, 50, replace=False)] = np.iinfo(np.int32).max
+    g = amb.Population("wealth", n, seed=4)
+    o = oracle.Population("wealth", n, seed=4)
+    g.write("wealth", torch.from_numpy(w0).cuda())
+    o.w[:] = w0
+    g.step(12)
+    o.step(12)
+    assert np.array_equal(host(g.column("wealth")), o.w)
+    assert np.array_equal(g.counts(), o.counts())
+    g.close()
