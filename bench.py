@@ -48,6 +48,19 @@ def sir_layout_bytes_per_agent_step(n, L):
     return 16.0 + 4.0 * L * L / n
 
 
+def sir_config(world):
+    """The workload's config, the same on both arms: the 10M-agent SIR
+    population, one replicate per rank, and the working set against L2 (the
+    step's records and cell index, 227 MB, exceed the 129 MB L2, so no flush
+    is needed between timed steps)."""
+    c = SIR_CFG
+    return {"workload": "sir_10M_L4096", "n_agents": c["n"], "grid_side": c["L"], "beta": c["beta"],
+            "gamma": c["gamma"], "n_init_infected": c["n0"], "seed": c["seed"],
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": "working set %.0f MB > L2 129 MB (no flush needed)" % (
+                sir_layout_bytes_per_agent_step(c["n"], c["L"]) * c["n"] / 1e6)}
+
+
 def profiled(key, field="dram_bytes_per_launch"):
     """A per-launch figure of the kernel from the committed ncu capture (DRAM
     bytes read + written by default), or None when the kernel's sources
@@ -744,11 +757,8 @@ def gpu_arm(args):
         "vs_baseline": None,
         "dtype": "int32/u8",
         "data": "synthetic (seeded Philox initial state, no dataset)",
-        "config": {"workload": "sir_10M_L4096", "n_agents": n, "grid_side": L, "beta": SIR_CFG["beta"],
-                   "gamma": SIR_CFG["gamma"], "n_init_infected": SIR_CFG["n0"], "seed": SIR_CFG["seed"],
-                   "sir_path": path, "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "working set %.0f MB > L2 129 MB (no flush needed)" % (
-                       (b_layout * n) / 1e6)},
+        "config": sir_config(world),
+        "sir_path": path,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "peak_kind": peak_kind, "traffic": traffic, "bytes_per_agent_step": b_alg,
                      "layout_bytes_per_agent_step": b_layout, "layout_frac": b_layout * n / (step_ms / 1e3) / 1e9 / hbm,
@@ -805,8 +815,7 @@ def reference_arm(args):
         "vs_baseline": None,
         "dtype": "int32/u8",
         "data": "synthetic (seeded Philox initial state, no dataset)",
-        "config": {"workload": "sir_10M_L4096", "n_agents": c["n"], "grid_side": c["L"], "beta": c["beta"],
-                   "gamma": c["gamma"], "n_init_infected": c["n0"], "seed": c["seed"]},
+        "config": sir_config(world),
         "cpu_baseline": {"value": v, "unit": "agent-steps/s", "cores": 1, "kind": "oracle",
                          "sample": "steps %d..%d of the full 10M-agent population, one thread, as three runs of %d "
                                    "steps, slowest dropped, other two averaged" % (warm, warm + 3 * steps, steps),
