@@ -147,9 +147,7 @@ amb_status launch_scan(const int32_t *in, int32_t *out, int32_t *out2, uint32_t 
 //   [17:16] state                   [19:18] unused
 //   [21:20] next move dy + 1
 //   [22]    next-step recovery draw passed (infected agents)
-//   [30:23] next-step infection code (susceptible agents): 0 = not infected
-//           whatever k; c in 1..254 = infected iff k >= c; 255 = needs
-//           k >= 255 and the exact comparison (redrawn)
+//   [30:23] top byte of the next-step infection draw u1 (susceptible agents)
 //   [31]    always 0
 namespace amb {
 constexpr uint32_t kAuxXMask = 0xFFFFu;
@@ -158,8 +156,6 @@ constexpr int kAuxDxShift = 18;
 constexpr int kAuxDyShift = 20;
 constexpr int kAuxRecShift = 22;
 constexpr int kAuxCodeShift = 23;
-constexpr uint32_t kCodeExact = 255u;
-constexpr uint32_t kCodeTable = 254u;  // entries 1..254 of T_inf cached in shared memory
 }  // namespace amb
 
 struct amb_pop {

@@ -39,11 +39,11 @@
 // 32-bit counters per cell in a per-CTA slice of global memory instead (same
 // steps, exact for any density).
 //
-// Infection code.  kmin(u1) = the smallest k in [1, K] with u1 < T_inf[k]
-// (T_inf is non-decreasing), so "u1 < T_inf[min(k, K)]" is "k >= kmin".  It is
-// found through a 256-entry table indexed by the top byte of u1 that holds
-// the range of kmin over that byte's 2^24 values, then a binary search inside
-// the range (usually empty).
+// Infection test.  A susceptible agent's record holds the top byte of its
+// infection draw u1 for the step; with k infected agents in its new cell it
+// is infected iff u1 < T_inf[min(k, K)].  When the threshold lies outside
+// the byte's 2^24 values the byte decides; otherwise (about one test in 256)
+// the agent's Philox block is recomputed and u1 compared exactly.
 #pragma once
 
 #include "amb_internal.cuh"
@@ -58,7 +58,6 @@ constexpr int kMaxSrcRows = kMaxBandRows + 2;
 constexpr uint32_t kPackedLimit = 65536;       // records per band for 16-bit halves
 constexpr int kU1 = 8;                         // independent loads per thread, pass 1
 constexpr int kU2 = 4;                         // independent loads per thread, pass 2
-constexpr uint32_t kNoCode = 255u;             // search result "no k <= 254"
 
 struct BandArgs {
     const uint2 *rec_in;  // {id, word}
@@ -110,47 +109,16 @@ inline void round_keys(uint32_t k0, uint32_t k1, uint32_t *rk0, uint32_t *rk1)
     }
 }
 
-// Shared tables of the infection code: T_inf[min(k, K)] for k = 0 .. 254 and
-// the per-top-byte range of kmin, packed lo | hi << 8.
+// Shared table of the infection thresholds: tinf[k] = T_inf[min(k, K)] for
+// k = 0 .. 255 (larger k read the global table).
 struct CodeTables {
-    uint32_t tinf[kCodeTable + 2];
-    uint32_t range[256];
+    uint32_t tinf[256];
 };
-
-// first k in [lo, hi] (hi <= 255) with k == 255 or u < tinf[k]
-__device__ __forceinline__ uint32_t code_search(const uint32_t *tinf, uint32_t u, uint32_t lo, uint32_t hi)
-{
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;  // mid <= 254
-        if (u < tinf[mid])
-            hi = mid;
-        else
-            lo = mid + 1;
-    }
-    return lo;
-}
 
 __device__ __forceinline__ void load_code_tables(CodeTables &ct, const uint32_t *t_inf, uint32_t K)
 {
-    for (uint32_t i = threadIdx.x; i <= kCodeTable; i += blockDim.x) ct.tinf[i] = t_inf[i < K ? i : K];
+    for (uint32_t i = threadIdx.x; i < 256u; i += blockDim.x) ct.tinf[i] = t_inf[i < K ? i : K];
     __syncthreads();
-    for (uint32_t b = threadIdx.x; b < 256u; b += blockDim.x) {
-        const uint32_t lo = code_search(ct.tinf, b << 24, 1u, kNoCode);
-        const uint32_t hi = code_search(ct.tinf, (b << 24) | 0xFFFFFFu, 1u, kNoCode);
-        ct.range[b] = lo | (hi << 8);
-    }
-    __syncthreads();
-}
-
-// Infection code of a susceptible agent's next-step word u1.
-__device__ __forceinline__ uint32_t infection_code(const CodeTables &ct, uint32_t u1, uint32_t K, uint32_t tinf_max)
-{
-    const uint32_t r = ct.range[u1 >> 24];
-    uint32_t k = r & 0xFFu;
-    const uint32_t hi = r >> 8;
-    if (k != hi) k = code_search(ct.tinf, u1, k, hi);
-    if (k <= kCodeTable) return k;
-    return (K > kCodeTable && u1 < tinf_max) ? kCodeExact : 0u;
 }
 
 // v + (dp - 1) wrapped on a ring of L sites (v in [0, L), dp in {0, 1, 2})
@@ -178,24 +146,23 @@ static_assert(byte_table_matches(kDpxLo, kDpxHi, kDX) && byte_table_matches(kDpy
 
 // Record word of an agent at column x whose state (after this step) is st,
 // with its draws for step t: the column after its move, the move's dy, and
-// the infection code (susceptible) or recovery bit (infected).
-__device__ __forceinline__ uint32_t pack_record(const U4 &u, uint32_t st, uint32_t x, uint32_t L, const CodeTables &ct,
-                                                uint32_t K, uint32_t tinf_max, uint32_t t_rec)
+// the top byte of the infection draw u1 (susceptible) or the recovery bit
+// (infected).
+__device__ __forceinline__ uint32_t pack_record(const U4 &u, uint32_t st, uint32_t x, uint32_t L, uint32_t t_rec)
 {
     const uint32_t d = u.w0 >> 29;
     const uint32_t dpx = __byte_perm(kDpxLo, kDpxHi, d);
     const uint32_t dpy = __byte_perm(kDpyLo, kDpyHi, d);
     const uint32_t w = wrap_step(x, dpx, L) | (st << kAuxStateShift) | (dpy << kAuxDyShift);
-    const uint32_t code = infection_code(ct, u.w1, K, tinf_max) << kAuxCodeShift;
+    const uint32_t top = (u.w1 >> 24) << kAuxCodeShift;
     const uint32_t rec = (u.w2 < t_rec ? 1u : 0u) << kAuxRecShift;
-    return w | (st == AMB_S ? code : (st == AMB_I ? rec : 0u));
+    return w | (st == AMB_S ? top : (st == AMB_I ? rec : 0u));
 }
 
 __device__ __forceinline__ uint32_t record_word(uint32_t id, uint32_t t, uint32_t st, uint32_t x, uint32_t L,
-                                                const uint32_t *rk0, const uint32_t *rk1, const CodeTables &ct,
-                                                uint32_t K, uint32_t tinf_max, uint32_t t_rec)
+                                                const uint32_t *rk0, const uint32_t *rk1, uint32_t t_rec)
 {
-    return pack_record(philox_rk(id, t, rk0, rk1), st, x, L, ct, K, tinf_max, t_rec);
+    return pack_record(philox_rk(id, t, rk0, rk1), st, x, L, t_rec);
 }
 
 // Loads of data that the launch itself never writes (__ldg, the read-only
@@ -326,21 +293,23 @@ __device__ __noinline__ bool exact_infection(const BandArgs &a, uint32_t id, uin
 }
 
 template <bool kParamKeys, class Ctr>
-__device__ __forceinline__ uint32_t new_state(const BandArgs &a, const Ctr &ctr, uint32_t c, uint32_t w, uint32_t id,
-                                              Tally &tl)
+__device__ __forceinline__ uint32_t new_state(const BandArgs &a, const CodeTables &ct, const Ctr &ctr, uint32_t c,
+                                              uint32_t w, uint32_t id, Tally &tl)
 {
     uint32_t st = (w >> kAuxStateShift) & 3u;
     if (st == AMB_S) {
-        const uint32_t code = (w >> kAuxCodeShift) & 0xFFu;
-        if (code != 0u) {
-            const uint32_t k = ctr.infected(c);
-            if (k >= code) {
-                bool hit = true;
-                if (code == kCodeExact) hit = exact_infection<kParamKeys>(a, id, k);
-                if (hit) {
-                    st = AMB_I;
-                    ++tl.fresh;
-                }
+        const uint32_t k = ctr.infected(c);
+        if (k != 0u) {
+            // infected iff u1 < T = T_inf[min(k, K)]; the record holds the top
+            // byte of u1: every u1 with that byte is below T, none is, or T
+            // lies inside the byte's range and the draw is redone exactly
+            const uint32_t T = k < 256u ? ct.tinf[k] : a.t_inf[k < a.K ? k : a.K];
+            const uint32_t lo = ((w >> kAuxCodeShift) & 0xFFu) << 24;
+            bool hit = (lo | 0xFFFFFFu) < T;
+            if (!hit && lo < T) hit = exact_infection<kParamKeys>(a, id, k);
+            if (hit) {
+                st = AMB_I;
+                ++tl.fresh;
             }
         }
     } else if (st == AMB_I) {
@@ -378,7 +347,7 @@ __device__ __forceinline__ void prefetch_band(const BandArgs &a, uint32_t b, boo
 
 template <bool kParamKeys, bool kCoherent, class Ctr>
 __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, const Ctr &ctr, uint32_t b, uint32_t r0,
-                                          uint32_t r1, uint32_t M, uint32_t tinf_max, Tally &tl)
+                                          uint32_t r1, uint32_t M, Tally &tl)
 {
     const uint32_t L = a.L;
     const uint32_t rows = r1 - r0;
@@ -539,7 +508,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
                 st[u] = 0u;
                 slot[u] = 0u;
                 if (ok[u]) {
-                    st[u] = new_state<kParamKeys>(a, ctr, c, w, ids[u], tl);
+                    st[u] = new_state<kParamKeys>(a, sh.ct, ctr, c, w, ids[u], tl);
                     slot[u] = P + ctr.take(c);
                 }
                 if (ok[u] && slot[u] >= a.n) {
@@ -554,7 +523,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
             for (int u = 0; u < kU2; ++u) {
                 if (!ok[u]) continue;
                 a.rec_out[slot[u]] =
-                    make_uint2(ids[u], pack_record(r[u], st[u], aux[u] & kAuxXMask, L, sh.ct, a.K, tinf_max, a.t_rec));
+                    make_uint2(ids[u], pack_record(r[u], st[u], aux[u] & kAuxXMask, L, a.t_rec));
             }
         }
     }
@@ -566,7 +535,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
 // counters).  prefetch: pull band b + gridDim.x into L2 meanwhile.
 template <bool kParamKeys, bool kCoherent>
 __device__ __forceinline__ void process_band(const BandArgs &a, BandShared &sh, uint32_t *band_smem,
-                                             uint32_t *wide_slice, uint32_t b, uint32_t tinf_max, bool prefetch,
+                                             uint32_t *wide_slice, uint32_t b, bool prefetch,
                                              Tally &tl)
 {
     const uint32_t L = a.L, tid = threadIdx.x;
@@ -606,9 +575,9 @@ __device__ __forceinline__ void process_band(const BandArgs &a, BandShared &sh, 
     }
     __syncthreads();
     if (M < kPackedLimit || wide_slice == nullptr)
-        band_body<kParamKeys, kCoherent>(a, sh, PackedCtr{band_smem}, b, r0, r1, M, tinf_max, tl);
+        band_body<kParamKeys, kCoherent>(a, sh, PackedCtr{band_smem}, b, r0, r1, M, tl);
     else
-        band_body<kParamKeys, kCoherent>(a, sh, WideCtr{wide_slice, wide_slice + (size_t)a.H * L}, b, r0, r1, M, tinf_max, tl);
+        band_body<kParamKeys, kCoherent>(a, sh, WideCtr{wide_slice, wide_slice + (size_t)a.H * L}, b, r0, r1, M, tl);
 }
 
 // All threads: add the block's tally to row[0..3] and clear it.

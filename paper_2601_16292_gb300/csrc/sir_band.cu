@@ -18,7 +18,6 @@ __global__ void __launch_bounds__(kBandNT, kBandCtasPerSm) sir_band_kernel(const
     if (blockIdx.x == 0 && tid == 0) a.tickets[a.parity ^ 1u] = 0ull;
     if (tid < 4) sh.cnt[tid] = 0ull;
     load_code_tables(sh.ct, a.t_inf, a.K);
-    const uint32_t tinf_max = a.t_inf[a.K];
     Tally tl = {0u, 0u, 0u, 0u};
     uint32_t *wide_slice = a.wide ? a.wide + (size_t)blockIdx.x * 2u * a.H * a.L : nullptr;
     for (;;) {
@@ -26,7 +25,7 @@ __global__ void __launch_bounds__(kBandNT, kBandCtasPerSm) sir_band_kernel(const
         __syncthreads();
         const uint32_t b = sh.band;
         if (b >= a.n_bands) break;
-        process_band<true, false>(a, sh, band_smem, wide_slice, b, tinf_max, true, tl);
+        process_band<true, false>(a, sh, band_smem, wide_slice, b, true, tl);
     }
     flush_tally(sh, tl, a.row);
 }
@@ -41,21 +40,16 @@ struct BuildArgs {
     uint2 *rec;
     uint32_t t;
     uint32_t rk0[10], rk1[10];
-    const uint32_t *t_inf;
-    uint32_t K, t_rec;
+    uint32_t t_rec;
 };
 
 __global__ void band_build_kernel(const BuildArgs a)
 {
-    __shared__ CodeTables ct;
-    load_code_tables(ct, a.t_inf, a.K);
-    const uint32_t tinf_max = a.t_inf[a.K];
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < a.n; s += gridDim.x * blockDim.x) {
         const uint32_t id = (uint32_t)a.ids[s];
         if (id >= a.n) continue;  // only slots of agents left out of the index
         const uint32_t st = a.state[id];
-        a.rec[s] = make_uint2(id, record_word(id, a.t, st, (uint32_t)a.x[id], a.L, a.rk0, a.rk1, ct, a.K, tinf_max,
-                                              a.t_rec));
+        a.rec[s] = make_uint2(id, record_word(id, a.t, st, (uint32_t)a.x[id], a.L, a.rk0, a.rk1, a.t_rec));
     }
 }
 
@@ -215,8 +209,6 @@ amb_status sir_band_init(amb_pop *pop, const int32_t *x, const int32_t *y, const
         b.rec = pop->rec[nb];
         b.t = (uint32_t)pop->t;
         round_keys(pop->key0, pop->key1, b.rk0, b.rk1);
-        b.t_inf = pop->t_inf_d;
-        b.K = pop->K;
         b.t_rec = pop->t_rec;
         band_build_kernel<<<grid_for(n, 256, 8u), 256, 0, s>>>(b);
     }
