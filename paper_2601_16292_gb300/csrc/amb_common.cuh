@@ -181,19 +181,22 @@ __device__ __forceinline__ uint32_t lookback_exclusive(uint64_t *status, uint32_
     return excl;
 }
 
-// One warp (all 32 lanes): publish the tile's aggregate, walk back 32
-// predecessors at a time (one ballot per 32 status words), publish the
-// inclusive prefix and return the exclusive prefix (all lanes).
+// One thread: publish the tile's aggregate (tile 0: its inclusive prefix),
+// so that successors can walk past it before it knows its own prefix.
+__device__ __forceinline__ void lookback_publish(uint64_t *status, uint32_t tile, uint32_t epoch, uint32_t aggregate)
+{
+    status_store(&status[tile], status_word(epoch, tile == 0 ? kFlagPrefix : kFlagAgg, aggregate));
+}
+
+// One warp (all 32 lanes), after lookback_publish of the same tile: walk
+// back 32 predecessors at a time (one ballot per 32 status words), publish
+// the inclusive prefix and return the exclusive prefix (all lanes).
 // Bounded like lookback_exclusive (timer + shared error word).
-__device__ __forceinline__ uint32_t warp_lookback(uint64_t *status, uint32_t tile, uint32_t epoch, uint32_t aggregate,
+__device__ __forceinline__ uint32_t lookback_wait(uint64_t *status, uint32_t tile, uint32_t epoch, uint32_t aggregate,
                                                   uint32_t *err)
 {
     const uint32_t lane = threadIdx.x & 31u;
-    if (tile == 0) {
-        if (lane == 0) status_store(&status[0], status_word(epoch, kFlagPrefix, aggregate));
-        return 0u;
-    }
-    if (lane == 0) status_store(&status[tile], status_word(epoch, kFlagAgg, aggregate));
+    if (tile == 0) return 0u;
     uint32_t excl = 0;
     int64_t base = (int64_t)tile - 1;
     uint32_t spins = 0;
@@ -231,6 +234,14 @@ __device__ __forceinline__ uint32_t warp_lookback(uint64_t *status, uint32_t til
     }
     if (lane == 0) status_store(&status[tile], status_word(epoch, kFlagPrefix, excl + aggregate));
     return excl;
+}
+
+// One warp: lookback_publish by lane 0, then lookback_wait.
+__device__ __forceinline__ uint32_t warp_lookback(uint64_t *status, uint32_t tile, uint32_t epoch, uint32_t aggregate,
+                                                  uint32_t *err)
+{
+    if ((threadIdx.x & 31u) == 0) lookback_publish(status, tile, epoch, aggregate);
+    return lookback_wait(status, tile, epoch, aggregate, err);
 }
 
 // ------------------------------------------------------------ block scan ---

@@ -22,13 +22,11 @@
 //      (bands are handed out in order by an atomic ticket);
 //   3. writes start[] for its cells and row_start for its rows;
 //   4. reads the records again (now from L2) and, for each agent landing in
-//      the band, applies infection (k >= the agent's precomputed code) or
-//      recovery, draws the agent's next-step Philox words (move, and the
-//      infection code or recovery bit its new state needs) and scatters the
-//      record to its new slot.
-// While a CTA works on band b it has the bulk-copy engine prefetch into L2 the
-// records of band b + gridDim.x, the band the next round of tickets is likely
-// to hand it (a guess: a wrong one warms L2 for another CTA).
+//      the band, applies infection (its infection draw against the threshold
+//      for the k infected agents of its new cell) or recovery, draws the
+//      agent's next-step Philox block (move, and the top byte of the
+//      infection draw or the recovery bit its new state needs) and scatters
+//      the record to its new slot.
 // Per-step S / I / R / new-infection counts are warp-aggregated.
 //
 // Counters.  A band whose source rows hold fewer than 65,536 records keeps
@@ -281,10 +279,10 @@ __device__ __forceinline__ U4 agent_draws(const BandArgs &a, uint32_t id, uint32
         return philox(id, t, a.k0, a.k1);
 }
 
-// The exact infection test of an agent whose code says k >= 255 infected
-// agents are needed: its draw u1 for step t against T_inf[min(k, K)].  Kept
-// out of line: it is rare, and inlined its Philox block would raise the
-// register demand of the whole record loop.
+// The exact infection test of an agent whose recorded top byte of u1 cannot
+// decide: its draw u1 for step t against T_inf[min(k, K)].  Kept out of
+// line: it is rare, and inlined its Philox block would raise the register
+// demand of the whole record loop.
 template <bool kParamKeys>
 __device__ __noinline__ bool exact_infection(const BandArgs &a, uint32_t id, uint32_t k)
 {
@@ -321,28 +319,12 @@ __device__ __forceinline__ uint32_t new_state(const BandArgs &a, const CodeTable
     return st;
 }
 
-// L2 prefetch of global memory by the bulk-copy engine (16-byte aligned
-// start, size a multiple of 16)
-__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
+// Band row a record lands in: byte (dy + 1) of its source row's table (0xFF
+// when outside the band, also for the sentinel word 0xFFFFFFFF, whose dy
+// field reads 3).
+__device__ __forceinline__ uint32_t dest_row(uint32_t tab, uint32_t w)
 {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
-// Warp 0: prefetch into L2 the records of the source rows of band b.  Record
-// arrays are allocated with 2 spare entries, so widening a row's range to
-// 16-byte boundaries stays inside them.
-__device__ __forceinline__ void prefetch_band(const BandArgs &a, uint32_t b, bool single)
-{
-    const uint32_t L = a.L;
-    const uint32_t r0 = (uint32_t)(((uint64_t)b * L) / a.n_bands);
-    const uint32_t r1 = (uint32_t)(((uint64_t)(b + 1u) * L) / a.n_bands);
-    const uint32_t nsrc = single ? L : (r1 - r0) + 2u;
-    for (uint32_t j = threadIdx.x; j < nsrc; j += 32u) {
-        const uint32_t y = single ? j : (r0 + L - 1u + j) % L;
-        const uint32_t s0 = (uint32_t)a.row_in[y] & ~1u;
-        const uint32_t s1 = ((uint32_t)a.row_in[y + 1] + 1u) & ~1u;
-        if (s1 > s0) prefetch_l2(a.rec_in + s0, (s1 - s0) * 8u);
-    }
+    return __byte_perm(tab, 0u, ((w >> kAuxDyShift) & 3u) | 0x4440u);
 }
 
 template <bool kParamKeys, bool kCoherent, class Ctr>
@@ -354,11 +336,13 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
     const uint32_t cells = rows * L;
     const uint32_t tid = threadIdx.x;
     ctr.zero(cells);
+    if (tid == 0) sh.total = 0u;
     __syncthreads();
 
     // pass 1: agents and start-of-step infected per new cell of the band
     {
-        uint32_t j = 0;  // source row of the thread's current record (never decreases)
+        uint32_t landed = 0;  // the thread's records that land in the band
+        uint32_t j = 0;       // source row of the thread's current record (never decreases)
         uint4 ri = sh.rows[0];
         for (uint32_t v0 = tid; v0 < M; v0 += kBandNT * kU1) {
             uint32_t aux[kU1], yy[kU1];
@@ -382,13 +366,20 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
                     atomicOr(a.err, ERR_RANGE);
                     continue;
                 }
-                const uint32_t yo = (yy[u] >> (8u * ((w >> kAuxDyShift) & 3u))) & 0xFFu;
+                const uint32_t yo = dest_row(yy[u], w);
                 if (yo >= rows) continue;  // lands outside the band
+                ++landed;
                 ctr.add(yo * L + xn, ((w >> kAuxStateShift) & 3u) == AMB_I);
             }
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) landed += __shfl_xor_sync(0xffffffffu, landed, o);
+        if ((tid & 31u) == 0 && landed) atomicAdd(&sh.total, landed);
     }
     __syncthreads();
+    // the band's total is known now: publish it at once, so that successors
+    // waiting in look-back see it while this band still scans
+    if (tid == 0) lookback_publish(a.status, b, a.epoch, sh.total);
 
     // scan of the band's counts: every warp owns a run of consecutive cells
     // (groups of four); (a) warp totals, (b) warp 0 scans them and gets the
@@ -420,7 +411,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
             if (lane >= (uint32_t)o) incl += t;
         }
         const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
-        const uint32_t P = warp_lookback(a.status, b, a.epoch, T, a.err);
+        const uint32_t P = lookback_wait(a.status, b, a.epoch, T, a.err);
         if (lane < kWarps) sh.warp[lane] = incl - v;
         if (lane == 0) {
             sh.prefix = P;
@@ -485,7 +476,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
                 const uint32_t v = v0 + (uint32_t)u * kBandNT;
                 aux[u] = 0xFFFFFFFFu;
                 ids[u] = 0u;
-                yy[u] = 0u;
+                yy[u] = 0xFFFFFFFFu;
                 if (v < M) {
                     while (ri.x <= v) ri = sh.rows[++j];
                     yy[u] = ri.z;
@@ -502,8 +493,8 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
             for (int u = 0; u < kU2; ++u) {
                 const uint32_t w = aux[u];
                 const uint32_t xn = w & kAuxXMask;
-                const uint32_t yo = (yy[u] >> (8u * ((w >> kAuxDyShift) & 3u))) & 0xFFu;
-                ok[u] = (w != 0xFFFFFFFFu) && (xn < L) && (yo < rows);
+                const uint32_t yo = dest_row(yy[u], w);
+                ok[u] = (xn < L) && (yo < rows);  // the sentinel word lands nowhere
                 const uint32_t c = yo * L + xn;
                 st[u] = 0u;
                 slot[u] = 0u;
@@ -532,19 +523,13 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
 
 // All threads: band b of the step described by `a` (its source-row tables,
 // then band_body with shared-memory or, for very dense bands, global
-// counters).  prefetch: pull band b + gridDim.x into L2 meanwhile.
+// counters).
 template <bool kParamKeys, bool kCoherent>
 __device__ __forceinline__ void process_band(const BandArgs &a, BandShared &sh, uint32_t *band_smem,
-                                             uint32_t *wide_slice, uint32_t b, bool prefetch,
-                                             Tally &tl)
+                                             uint32_t *wide_slice, uint32_t b, Tally &tl)
 {
     const uint32_t L = a.L, tid = threadIdx.x;
     const bool single = (a.n_bands == 1);
-    // the band the next wave of tickets is likely to give this CTA: have its
-    // records pulled into L2 while this one is processed (a guess; a wrong
-    // guess only warms L2 for another CTA)
-    const uint32_t ahead = b + gridDim.x;
-    if (prefetch && tid < 32 && ahead < a.n_bands) prefetch_band(a, ahead, single);
     // bands of floor / ceil(L / n_bands) rows
     const uint32_t r0 = (uint32_t)(((uint64_t)b * L) / a.n_bands);
     const uint32_t r1 = (uint32_t)(((uint64_t)(b + 1u) * L) / a.n_bands);
@@ -566,7 +551,7 @@ __device__ __forceinline__ void process_band(const BandArgs &a, BandShared &sh, 
     if (tid < nsrc) {
         // record v of the band's source sequence with off <= v < off + len
         // sits at slot v + (beg - off) (modulo 2^32)
-        uint32_t tab = 0;
+        uint32_t tab = 0xFF000000u;  // byte 3: the dy field 3 of the sentinel word lands nowhere
         for (uint32_t dp = 0; dp < 3u; ++dp) {
             const uint32_t yo = wrap_step(y, dp, L) - r0;  // wraps above 0xFF when outside
             tab |= (yo < r1 - r0 ? yo : 0xFFu) << (8u * dp);

@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(kBandNT, 1) persist_kernel(const PersistArgs p
             __syncthreads();
             if (tid == 0) s_code_job = e.job;
             const BandArgs &a = s_sir.a;
-            process_band<false, true>(a, sh, dyn_smem, wide_slice, u, false, tl);
+            process_band<false, true>(a, sh, dyn_smem, wide_slice, u, tl);
             flush_tally(sh, tl, a.row);
         } else if (e.kind == kKindWalk) {
             if (fresh_desc) load_l2(s_walk, &pa.walk[e.job]);

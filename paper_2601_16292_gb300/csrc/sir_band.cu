@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(kBandNT, kBandCtasPerSm) sir_band_kernel(const
         __syncthreads();
         const uint32_t b = sh.band;
         if (b >= a.n_bands) break;
-        process_band<true, false>(a, sh, band_smem, wide_slice, b, true, tl);
+        process_band<true, false>(a, sh, band_smem, wide_slice, b, tl);
     }
     flush_tally(sh, tl, a.row);
 }
