@@ -54,8 +54,8 @@ constexpr uint32_t kBandSmem = 224u * 1024u;  // dynamic shared memory per CTA (
 constexpr uint32_t kMaxBandRows = 32;          // tallest band (source-row tables are static)
 constexpr int kMaxSrcRows = kMaxBandRows + 2;
 constexpr uint32_t kPackedLimit = 65536;       // records per band for 16-bit halves
-constexpr int kU1 = 8;                         // independent loads per thread, pass 1
-constexpr int kU2 = 4;                         // independent loads per thread, pass 2
+constexpr int kU1 = 4;                         // loads per thread and group, pass 1 (two groups in flight)
+constexpr int kU2 = 3;                         // loads per thread and group, pass 2 (two groups in flight)
 
 struct BandArgs {
     const uint2 *rec_in;  // {id, word}
@@ -339,13 +339,15 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
     if (tid == 0) sh.total = 0u;
     __syncthreads();
 
-    // pass 1: agents and start-of-step infected per new cell of the band
+    // pass 1: agents and start-of-step infected per new cell of the band.
+    // A thread takes records v0 + u * kBandNT (u < kU1) per group; two
+    // register sets let the loads of the next group fly while the current
+    // one is counted.
     {
         uint32_t landed = 0;  // the thread's records that land in the band
         uint32_t j = 0;       // source row of the thread's current record (never decreases)
         uint4 ri = sh.rows[0];
-        for (uint32_t v0 = tid; v0 < M; v0 += kBandNT * kU1) {
-            uint32_t aux[kU1], yy[kU1];
+        auto fetch = [&](uint32_t v0, uint32_t(&aux)[kU1], uint32_t(&yy)[kU1]) {
 #pragma unroll
             for (int u = 0; u < kU1; ++u) {
                 const uint32_t v = v0 + (uint32_t)u * kBandNT;
@@ -357,6 +359,8 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
                     aux[u] = ld_nc<kCoherent>(&a.rec_in[v + ri.y].y);
                 }
             }
+        };
+        auto count = [&](const uint32_t(&aux)[kU1], const uint32_t(&yy)[kU1]) {
 #pragma unroll
             for (int u = 0; u < kU1; ++u) {
                 const uint32_t w = aux[u];
@@ -371,6 +375,16 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
                 ++landed;
                 ctr.add(yo * L + xn, ((w >> kAuxStateShift) & 3u) == AMB_I);
             }
+        };
+        constexpr uint32_t G = kBandNT * kU1;
+        uint32_t auxA[kU1], yyA[kU1], auxB[kU1], yyB[kU1];
+        fetch(tid, auxA, yyA);
+        for (uint32_t v0 = tid; v0 < M; v0 += 2u * G) {
+            fetch(v0 + G, auxB, yyB);
+            count(auxA, yyA);
+            if (v0 + G >= M) break;
+            fetch(v0 + 2u * G, auxA, yyA);
+            count(auxB, yyB);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) landed += __shfl_xor_sync(0xffffffffu, landed, o);
@@ -465,12 +479,12 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
     }
     __syncthreads();
 
-    // pass 2: transitions, next draws, scatter (the records come from L2)
+    // pass 2: transitions, next draws, scatter (the records come from L2),
+    // with the loads of the next group in flight as in pass 1
     {
         uint32_t j = 0;
         uint4 ri = sh.rows[0];
-        for (uint32_t v0 = tid; v0 < M; v0 += kBandNT * kU2) {
-            uint32_t aux[kU2], yy[kU2], ids[kU2];
+        auto fetch = [&](uint32_t v0, uint32_t(&ids)[kU2], uint32_t(&aux)[kU2], uint32_t(&yy)[kU2]) {
 #pragma unroll
             for (int u = 0; u < kU2; ++u) {
                 const uint32_t v = v0 + (uint32_t)u * kBandNT;
@@ -485,7 +499,9 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
                     aux[u] = rv.y;
                 }
             }
-            // in phases over the thread's records, so that their Philox
+        };
+        auto update = [&](const uint32_t(&ids)[kU2], const uint32_t(&aux)[kU2], const uint32_t(&yy)[kU2]) {
+            // in phases over the group's records, so that their Philox
             // blocks are independent instruction streams
             uint32_t slot[kU2], st[kU2];
             bool ok[kU2];
@@ -513,9 +529,18 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
 #pragma unroll
             for (int u = 0; u < kU2; ++u) {
                 if (!ok[u]) continue;
-                a.rec_out[slot[u]] =
-                    make_uint2(ids[u], pack_record(r[u], st[u], aux[u] & kAuxXMask, L, a.t_rec));
+                a.rec_out[slot[u]] = make_uint2(ids[u], pack_record(r[u], st[u], aux[u] & kAuxXMask, L, a.t_rec));
             }
+        };
+        constexpr uint32_t G = kBandNT * kU2;
+        uint32_t idsA[kU2], auxA[kU2], yyA[kU2], idsB[kU2], auxB[kU2], yyB[kU2];
+        fetch(tid, idsA, auxA, yyA);
+        for (uint32_t v0 = tid; v0 < M; v0 += 2u * G) {
+            fetch(v0 + G, idsB, auxB, yyB);
+            update(idsA, auxA, yyA);
+            if (v0 + G >= M) break;
+            fetch(v0 + 2u * G, idsA, auxA, yyA);
+            update(idsB, auxB, yyB);
         }
     }
     __syncthreads();
