@@ -327,7 +327,7 @@ __device__ __forceinline__ uint32_t dest_row(uint32_t tab, uint32_t w)
     return __byte_perm(tab, 0u, ((w >> kAuxDyShift) & 3u) | 0x4440u);
 }
 
-template <bool kParamKeys, bool kCoherent, class Ctr>
+template <bool kParamKeys, bool kCoherent, bool kTicketAhead, class Ctr>
 __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, const Ctr &ctr, uint32_t b, uint32_t r0,
                                           uint32_t r1, uint32_t M, Tally &tl)
 {
@@ -479,6 +479,11 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
     }
     __syncthreads();
 
+    // the band this CTA takes next (sir_band_kernel reads it after the
+    // band): its ticket's latency hides behind pass 2
+    if constexpr (kTicketAhead)
+        if (tid == 0) sh.band = (uint32_t)atomicAdd(&a.tickets[a.parity], 1ull);
+
     // pass 2: transitions, next draws, scatter (the records come from L2),
     // with the loads of the next group in flight as in pass 1
     {
@@ -548,8 +553,9 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
 
 // All threads: band b of the step described by `a` (its source-row tables,
 // then band_body with shared-memory or, for very dense bands, global
-// counters).
-template <bool kParamKeys, bool kCoherent>
+// counters).  kTicketAhead: thread 0 draws the ticket of the CTA's next band
+// into sh.band when pass 2 starts.
+template <bool kParamKeys, bool kCoherent, bool kTicketAhead = false>
 __device__ __forceinline__ void process_band(const BandArgs &a, BandShared &sh, uint32_t *band_smem,
                                              uint32_t *wide_slice, uint32_t b, Tally &tl)
 {
@@ -585,9 +591,10 @@ __device__ __forceinline__ void process_band(const BandArgs &a, BandShared &sh, 
     }
     __syncthreads();
     if (M < kPackedLimit || wide_slice == nullptr)
-        band_body<kParamKeys, kCoherent>(a, sh, PackedCtr{band_smem}, b, r0, r1, M, tl);
+        band_body<kParamKeys, kCoherent, kTicketAhead>(a, sh, PackedCtr{band_smem}, b, r0, r1, M, tl);
     else
-        band_body<kParamKeys, kCoherent>(a, sh, WideCtr{wide_slice, wide_slice + (size_t)a.H * L}, b, r0, r1, M, tl);
+        band_body<kParamKeys, kCoherent, kTicketAhead>(a, sh, WideCtr{wide_slice, wide_slice + (size_t)a.H * L}, b, r0, r1,
+                                                       M, tl);
 }
 
 // All threads: add the block's tally to row[0..3] and clear it.

@@ -20,13 +20,14 @@ __global__ void __launch_bounds__(kBandNT, kBandCtasPerSm) sir_band_kernel(const
     load_code_tables(sh.ct, a.t_inf, a.K);
     Tally tl = {0u, 0u, 0u, 0u};
     uint32_t *wide_slice = a.wide ? a.wide + (size_t)blockIdx.x * 2u * a.H * a.L : nullptr;
-    for (;;) {
-        if (tid == 0) sh.band = (uint32_t)atomicAdd(&a.tickets[a.parity], 1ull);
-        __syncthreads();
-        const uint32_t b = sh.band;
-        if (b >= a.n_bands) break;
-        process_band<true, false>(a, sh, band_smem, wide_slice, b, tl);
-    }
+    // Bands are handed out in increasing order by ticket.  A CTA draws the
+    // ticket of its next band during the current band's pass 2; the smallest
+    // unfinished band is always some CTA's current one (all CTAs are
+    // resident), so every look-back ends.
+    if (tid == 0) sh.band = (uint32_t)atomicAdd(&a.tickets[a.parity], 1ull);
+    __syncthreads();
+    for (uint32_t b = sh.band; b < a.n_bands; b = sh.band)
+        process_band<true, false, true>(a, sh, band_smem, wide_slice, b, tl);
     flush_tally(sh, tl, a.row);
 }
 
@@ -178,8 +179,7 @@ amb_status sir_band_init(amb_pop *pop, const int32_t *x, const int32_t *y, const
     pop->band_grid = std::min<uint32_t>(g.n_bands, grid_max);
     pop->band_smem = g.smem;
     for (int b = 0; b < 2; ++b) {
-        // 4 spare entries: the step reads records in aligned groups of four
-        // (32 bytes), and L2 prefetches widen a row to 16-byte boundaries
+        // 4 spare entries past the last record (slack; no kernel reads them)
         if (!pop->rec[b]) AMB_TRY(dalloc(&pop->rec[b], (size_t)n + 4u, s));
         if (!pop->row_start[b]) AMB_TRY(dalloc(&pop->row_start[b], (size_t)L + 1, s));
     }
