@@ -71,7 +71,12 @@ enum { AMB_S = 0, AMB_I = 1, AMB_R = 2 };
 enum {
     AMB_SIR_AUTO = 0,    /* band path when the grid allows it, else generic */
     AMB_SIR_GENERIC = 1, /* id-ordered columns, global counting sort each step */
-    AMB_SIR_BAND = 2     /* cell-ordered records, one fused kernel per step */
+    AMB_SIR_BAND = 2,    /* cell-ordered records, one fused kernel per step */
+    AMB_SIR_BAND32 = 3,  /* band path with 32-bit per-cell counters in shared memory */
+    AMB_SIR_BAND16 = 4   /* band path with 16-bit per-cell counters (bands twice as tall; a band whose counts
+                            do not fit is redone with 32-bit counters); L a multiple of 8, at most 8192.
+                            AMB_SIR_BAND and AMB_SIR_AUTO take 16-bit counters when that needs fewer waves
+                            of bands and rows hold at most 3,072 agents on average */
 };
 
 typedef struct {

@@ -24,7 +24,7 @@ MODELS = {"wealth": AMB_WEALTH, "walk": AMB_WALK, "sir": AMB_SIR, "cwalk": AMB_C
 AMB_COL_WEALTH, AMB_COL_X, AMB_COL_Y, AMB_COL_STATE, AMB_COL_DAYS = 0, 1, 2, 3, 4
 COLUMNS = {"wealth": AMB_COL_WEALTH, "x": AMB_COL_X, "y": AMB_COL_Y, "state": AMB_COL_STATE, "days": AMB_COL_DAYS}
 AMB_S, AMB_I, AMB_R = 0, 1, 2
-AMB_SIR_AUTO, AMB_SIR_GENERIC, AMB_SIR_BAND = 0, 1, 2
+AMB_SIR_AUTO, AMB_SIR_GENERIC, AMB_SIR_BAND, AMB_SIR_BAND32, AMB_SIR_BAND16 = 0, 1, 2, 3, 4
 
 
 class AmbError(RuntimeError):

@@ -192,7 +192,8 @@ struct amb_pop {
     bool band_dirty = false;  // x, y, state hold written columns; records rebuilt before use
     uint32_t band_rows = 0, n_bands = 0;
     uint32_t band_grid = 0;
-    uint32_t *band_wide = nullptr;  // per-CTA 32-bit counters for bands too dense for 16-bit ones
+    uint32_t *band_wide = nullptr;  // per-CTA 32-bit counters in global memory (bands too dense for shared ones)
+    bool band_narrow = false;       // 16-bit shared counters (bands twice as tall)
     uint32_t band_smem = 0;         // dynamic shared memory of the step kernel (bytes)
 
     // SIR thresholds

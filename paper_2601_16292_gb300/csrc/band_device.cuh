@@ -63,7 +63,7 @@ struct BandArgs {
     uint2 *rec_out;
     int32_t *row_out;
     int32_t *start;
-    uint32_t *wide;  // 2 * H * L words per CTA, or null when n < kPackedLimit
+    uint32_t *wide;  // 2 * H * L words per CTA, or null when n < kPackedLimit and 32-bit shared counters are used
     uint32_t n, L, H, n_bands;
     uint32_t k0, k1, t;  // t = the step executed by this launch
     uint32_t rk0[10], rk1[10];  // Philox round keys of (k0, k1)
@@ -187,7 +187,14 @@ struct PackedCtr {
                 for (uint32_t e = i; e < cells; ++e) w[e] = 0u;
         }
     }
-    __device__ __forceinline__ void add(uint32_t c, bool infected) const { atomicAdd(&w[c], infected ? 0x10001u : 1u); }
+    static constexpr bool kNarrow = false;
+    // count an agent (and whether it is infected) in cell c; true when the
+    // counter overflowed (never, for these counters)
+    __device__ __forceinline__ bool add(uint32_t c, bool infected) const
+    {
+        atomicAdd(&w[c], infected ? 0x10001u : 1u);
+        return false;
+    }
     __device__ __forceinline__ uint32_t get(uint32_t i) const { return w[i] & 0xFFFFu; }
     __device__ __forceinline__ uint32_t infected(uint32_t c) const { return w[c] >> 16; }
     __device__ __forceinline__ uint32_t take(uint32_t c) const { return atomicAdd(&w[c], 1u) & 0xFFFFu; }
@@ -228,10 +235,12 @@ struct WideCtr {
         }
         __threadfence_block();
     }
-    __device__ __forceinline__ void add(uint32_t c, bool infected) const
+    static constexpr bool kNarrow = false;
+    __device__ __forceinline__ bool add(uint32_t c, bool infected) const
     {
         atomicAdd(&cnt[c], 1u);
         if (infected) atomicAdd(&inf[c], 1u);
+        return false;
     }
     __device__ __forceinline__ uint32_t get(uint32_t i) const { return cnt[i]; }
     __device__ __forceinline__ uint32_t infected(uint32_t c) const { return __ldcg(&inf[c]); }
@@ -250,6 +259,47 @@ struct WideCtr {
     }
 };
 
+// 16-bit counters, two cells per shared word (cell c in the half c & 1 of
+// word c >> 1).  While counting, bits [7:0] hold the cell's agents and
+// [15:8] its start-of-step infected agents; the scan turns them into the
+// cell's offset inside its band row (bits [11:0], then the slot cursor) and
+// the infected count (bits [15:12]).  A band fits when no cell holds 256
+// agents or 16 infected agents and no band row 4,096 agents; otherwise it is
+// redone with 32-bit counters.  Rows are a multiple of 8 cells long.
+struct NarrowCtr {
+    static constexpr bool kNarrow = true;
+    uint32_t *w;  // shared memory
+    __device__ __forceinline__ void zero(uint32_t cells) const
+    {
+        const uint32_t words = (cells + 1u) >> 1;
+        for (uint32_t i = threadIdx.x * 4u; i < words; i += kBandNT * 4u) {
+            if (i + 3u < words)
+                *reinterpret_cast<uint4 *>(&w[i]) = make_uint4(0u, 0u, 0u, 0u);
+            else
+                for (uint32_t e = i; e < words; ++e) w[e] = 0u;
+        }
+    }
+    // true when the cell's agent or infected count was already 255
+    __device__ __forceinline__ bool add(uint32_t c, bool infected) const
+    {
+        const uint32_t sh = (c & 1u) << 4;
+        const uint32_t old = atomicAdd(&w[c >> 1], (infected ? 0x101u : 1u) << sh) >> sh;
+        return (old & 0xFFu) == 0xFFu || (infected && (old & 0xFF00u) == 0xFF00u);
+    }
+    // the cell's half before taking a slot: cursor | infected count << 12
+    __device__ __forceinline__ uint32_t claim(uint32_t c) const
+    {
+        const uint32_t sh = (c & 1u) << 4;
+        return (atomicAdd(&w[c >> 1], 1u << sh) >> sh) & 0xFFFFu;
+    }
+};
+
+// The infected count of an agent's new cell, already known.
+struct KnownK {
+    uint32_t k;
+    __device__ __forceinline__ uint32_t infected(uint32_t) const { return k; }
+};
+
 struct BandShared {
     CodeTables ct;
     // per source row j of the band: {end of its records in the band's source
@@ -258,6 +308,8 @@ struct BandShared {
     uint4 rows[kMaxSrcRows];
     uint32_t warp[kBandNT / 32 + 1];
     uint32_t band, prefix, total;
+    uint32_t overflow;                // 16-bit counters: the band does not fit them
+    uint32_t rowbase[kMaxBandRows];   // 16-bit counters: each band row's first slot inside the band
     unsigned long long cnt[4];
 };
 
@@ -327,16 +379,22 @@ __device__ __forceinline__ uint32_t dest_row(uint32_t tab, uint32_t w)
     return __byte_perm(tab, 0u, ((w >> kAuxDyShift) & 3u) | 0x4440u);
 }
 
+// Returns false, before writing any record, when the band does not fit
+// 16-bit counters (the caller redoes it with 32-bit ones); true otherwise.
 template <bool kParamKeys, bool kCoherent, bool kTicketAhead, class Ctr>
-__device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, const Ctr &ctr, uint32_t b, uint32_t r0,
+__device__ __forceinline__ bool band_body(const BandArgs &a, BandShared &sh, const Ctr &ctr, uint32_t b, uint32_t r0,
                                           uint32_t r1, uint32_t M, Tally &tl)
 {
+    constexpr bool kNarrow = Ctr::kNarrow;
     const uint32_t L = a.L;
     const uint32_t rows = r1 - r0;
     const uint32_t cells = rows * L;
     const uint32_t tid = threadIdx.x;
     ctr.zero(cells);
-    if (tid == 0) sh.total = 0u;
+    if (tid == 0) {
+        sh.total = 0u;
+        sh.overflow = 0u;
+    }
     __syncthreads();
 
     // pass 1: agents and start-of-step infected per new cell of the band.
@@ -345,6 +403,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
     // one is counted.
     {
         uint32_t landed = 0;  // the thread's records that land in the band
+        bool ovf = false;     // a 16-bit counter overflowed
         uint32_t j = 0;       // source row of the thread's current record (never decreases)
         uint4 ri = sh.rows[0];
         auto fetch = [&](uint32_t v0, uint32_t(&aux)[kU1], uint32_t(&yy)[kU1]) {
@@ -373,7 +432,7 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
                 const uint32_t yo = dest_row(yy[u], w);
                 if (yo >= rows) continue;  // lands outside the band
                 ++landed;
-                ctr.add(yo * L + xn, ((w >> kAuxStateShift) & 3u) == AMB_I);
+                ovf |= ctr.add(yo * L + xn, ((w >> kAuxStateShift) & 3u) == AMB_I);
             }
         };
         constexpr uint32_t G = kBandNT * kU1;
@@ -389,95 +448,183 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) landed += __shfl_xor_sync(0xffffffffu, landed, o);
         if ((tid & 31u) == 0 && landed) atomicAdd(&sh.total, landed);
+        if (kNarrow && ovf) sh.overflow = 1u;
     }
     __syncthreads();
     // the band's total is known now: publish it at once, so that successors
     // waiting in look-back see it while this band still scans
     if (tid == 0) lookback_publish(a.status, b, a.epoch, sh.total);
+    if (kNarrow && sh.overflow) return false;
 
-    // scan of the band's counts: every warp owns a run of consecutive cells
-    // (groups of four); (a) warp totals, (b) warp 0 scans them and gets the
-    // band's first slot P by look-back, (c) every warp turns its counts into
-    // offsets and writes the cell index start[] = P + offset
-    constexpr uint32_t kWarps = kBandNT / 32;
-    static_assert(kWarps <= 32, "one warp scans the warp totals");
-    const uint32_t lane = tid & 31u, wid = tid >> 5;
-    const uint32_t quads = (cells + 3u) >> 2, qpw = (quads + kWarps - 1u) / kWarps;
-    const uint32_t q0 = wid * qpw, q1 = min(q0 + qpw, quads);
-    {
-        uint32_t part = 0;
-        for (uint32_t q = q0 + lane; q < q1; q += 32u) {
-            uint32_t c[4];
-            ctr.load4(q * 4u, cells, c);
-            part += Ctr::count_of(c[0]) + Ctr::count_of(c[1]) + Ctr::count_of(c[2]) + Ctr::count_of(c[3]);
-        }
+    if constexpr (kNarrow) {
+        // scan of the band's 16-bit counts, one warp per band row (rows <=
+        // 32): (a) row totals (two 16-bit lanes of a word accumulate without
+        // carries: a lane adds at most L/64 cells of at most 255 agents,
+        // L <= 8192); (b) warp 0 scans them into each row's first slot inside
+        // the band and gets the band's first slot P by look-back; (c) each
+        // warp turns its row's counts into offsets inside the row and writes
+        // the row's start[] = P + row base + offset
+        const uint32_t lane = tid & 31u, wid = tid >> 5;
+        const uint32_t wpr = L >> 1;  // words per row
+        if (wid < rows) {
+            const uint32_t *rw = ctr.w + wid * wpr;
+            uint32_t acc = 0;
+            for (uint32_t i = lane * 4u; i < wpr; i += 128u) {
+                const uint4 q = *reinterpret_cast<const uint4 *>(rw + i);
+                acc += (q.x & 0x00FF00FFu) + (q.y & 0x00FF00FFu) + (q.z & 0x00FF00FFu) + (q.w & 0x00FF00FFu);
+            }
+            uint32_t tot = (acc & 0xFFFFu) + (acc >> 16);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if (lane == 0) sh.warp[wid] = part;
-    }
-    __syncthreads();
-    if (wid == 0) {
-        const uint32_t v = lane < kWarps ? sh.warp[lane] : 0u;
-        uint32_t incl = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= (uint32_t)o) incl += t;
+            for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+            if (lane == 0) {
+                sh.rowbase[wid] = tot;
+                if (tot >= 4096u) sh.overflow = 1u;  // offsets inside the row need 12 bits
+            }
         }
-        const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
-        const uint32_t P = lookback_wait(a.status, b, a.epoch, T, a.err);
-        if (lane < kWarps) sh.warp[lane] = incl - v;
-        if (lane == 0) {
-            sh.prefix = P;
-            sh.total = T;
-        }
-    }
-    __syncthreads();
-    const uint32_t P = sh.prefix;
-    {
-        int32_t *start_band = a.start + (size_t)r0 * L;
-        const bool vec = (((size_t)r0 * L) & 3u) == 0;  // 16-byte aligned start[] stores
-        uint32_t run = sh.warp[wid];
-        for (uint32_t qb = q0; qb < q1; qb += 32u) {
-            const uint32_t q = qb + lane, i0 = q * 4u;
-            uint32_t c[4] = {0u, 0u, 0u, 0u};
-            if (q < q1) ctr.load4(i0, cells, c);
-            const uint32_t n0 = Ctr::count_of(c[0]), n1 = Ctr::count_of(c[1]), n2 = Ctr::count_of(c[2]);
-            const uint32_t s4 = n0 + n1 + n2 + Ctr::count_of(c[3]);
-            uint32_t incl = s4;
+        __syncthreads();
+        if (wid == 0) {
+            const uint32_t v = lane < rows ? sh.rowbase[lane] : 0u;
+            uint32_t incl = v;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= (uint32_t)o) incl += t;
             }
-            uint32_t off[4];
-            off[0] = run + incl - s4;
-            off[1] = off[0] + n0;
-            off[2] = off[1] + n1;
-            off[3] = off[2] + n2;
-            if (q < q1) {
-                ctr.store4(i0, cells, c, off);
-                if (vec && i0 + 3u < cells) {
-                    *reinterpret_cast<int4 *>(start_band + i0) =
-                        make_int4((int32_t)(P + off[0]), (int32_t)(P + off[1]), (int32_t)(P + off[2]),
-                                  (int32_t)(P + off[3]));
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (i0 + e < cells) start_band[i0 + e] = (int32_t)(P + off[e]);
-                }
+            const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
+            const uint32_t Pb = lookback_wait(a.status, b, a.epoch, T, a.err);
+            if (lane < rows) sh.rowbase[lane] = incl - v;
+            if (lane == 0) {
+                sh.prefix = Pb;
+                sh.total = T;
             }
-            run += __shfl_sync(0xffffffffu, incl, 31);
         }
+        __syncthreads();
+        if (sh.overflow) return false;
+        const uint32_t P = sh.prefix;
+        if (wid < rows) {
+            uint32_t *rw = ctr.w + wid * wpr;
+            const uint32_t base = P + sh.rowbase[wid];
+            int32_t *srow = a.start + (size_t)(r0 + wid) * L;
+            uint32_t run = 0, big = 0;
+            // 4 cells (2 words) per lane and step: 16-byte start[] stores,
+            // contiguous across the warp
+            for (uint32_t i0 = 0; i0 < wpr; i0 += 64u) {
+                const uint32_t i = i0 + lane * 2u;
+                const bool valid = i < wpr;
+                const uint2 q = valid ? *reinterpret_cast<const uint2 *>(rw + i) : make_uint2(0u, 0u);
+                const uint32_t n0 = q.x & 0xFFu, n1 = (q.x >> 16) & 0xFFu, n2 = q.y & 0xFFu, n3 = (q.y >> 16) & 0xFFu;
+                const uint32_t s4 = (n0 + n1) + (n2 + n3);
+                uint32_t incl = s4;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= (uint32_t)o) incl += t;
+                }
+                big |= (q.x | q.y) & 0xF000F000u;  // an infected count >= 16
+                const uint32_t o0 = run + incl - s4, o1 = o0 + n0, o2 = o1 + n1, o3 = o2 + n2;
+                if (valid) {
+                    *reinterpret_cast<uint2 *>(rw + i) = make_uint2(o0 | (o1 << 16) | ((q.x & 0x0F000F00u) << 4),
+                                                                    o2 | (o3 << 16) | ((q.y & 0x0F000F00u) << 4));
+                    *reinterpret_cast<int4 *>(srow + 2u * i) =
+                        make_int4((int32_t)(base + o0), (int32_t)(base + o1), (int32_t)(base + o2), (int32_t)(base + o3));
+                }
+                run += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            if (__any_sync(0xffffffffu, big != 0u) && lane == 0) sh.overflow = 1u;
+        }
+        if (tid < rows) a.row_out[r0 + tid] = (int32_t)(P + sh.rowbase[tid]);
+        if (b == a.n_bands - 1u && tid == 0) {
+            a.start[(size_t)L * L] = (int32_t)(P + sh.total);
+            a.row_out[L] = (int32_t)(P + sh.total);
+        }
+        __syncthreads();
+        if (sh.overflow) return false;
+    } else {
+        // scan of the band's counts: every warp owns a run of consecutive cells
+        // (groups of four); (a) warp totals, (b) warp 0 scans them and gets the
+        // band's first slot P by look-back, (c) every warp turns its counts into
+        // offsets and writes the cell index start[] = P + offset
+        constexpr uint32_t kWarps = kBandNT / 32;
+        static_assert(kWarps <= 32, "one warp scans the warp totals");
+        const uint32_t lane = tid & 31u, wid = tid >> 5;
+        const uint32_t quads = (cells + 3u) >> 2, qpw = (quads + kWarps - 1u) / kWarps;
+        const uint32_t q0 = wid * qpw, q1 = min(q0 + qpw, quads);
+        {
+            uint32_t part = 0;
+            for (uint32_t q = q0 + lane; q < q1; q += 32u) {
+                uint32_t c[4];
+                ctr.load4(q * 4u, cells, c);
+                part += Ctr::count_of(c[0]) + Ctr::count_of(c[1]) + Ctr::count_of(c[2]) + Ctr::count_of(c[3]);
+            }
+    #pragma unroll
+            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            if (lane == 0) sh.warp[wid] = part;
+        }
+        __syncthreads();
+        if (wid == 0) {
+            const uint32_t v = lane < kWarps ? sh.warp[lane] : 0u;
+            uint32_t incl = v;
+    #pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= (uint32_t)o) incl += t;
+            }
+            const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
+            const uint32_t P = lookback_wait(a.status, b, a.epoch, T, a.err);
+            if (lane < kWarps) sh.warp[lane] = incl - v;
+            if (lane == 0) {
+                sh.prefix = P;
+                sh.total = T;
+            }
+        }
+        __syncthreads();
+        const uint32_t P = sh.prefix;
+        {
+            int32_t *start_band = a.start + (size_t)r0 * L;
+            const bool vec = (((size_t)r0 * L) & 3u) == 0;  // 16-byte aligned start[] stores
+            uint32_t run = sh.warp[wid];
+            for (uint32_t qb = q0; qb < q1; qb += 32u) {
+                const uint32_t q = qb + lane, i0 = q * 4u;
+                uint32_t c[4] = {0u, 0u, 0u, 0u};
+                if (q < q1) ctr.load4(i0, cells, c);
+                const uint32_t n0 = Ctr::count_of(c[0]), n1 = Ctr::count_of(c[1]), n2 = Ctr::count_of(c[2]);
+                const uint32_t s4 = n0 + n1 + n2 + Ctr::count_of(c[3]);
+                uint32_t incl = s4;
+    #pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= (uint32_t)o) incl += t;
+                }
+                uint32_t off[4];
+                off[0] = run + incl - s4;
+                off[1] = off[0] + n0;
+                off[2] = off[1] + n1;
+                off[3] = off[2] + n2;
+                if (q < q1) {
+                    ctr.store4(i0, cells, c, off);
+                    if (vec && i0 + 3u < cells) {
+                        *reinterpret_cast<int4 *>(start_band + i0) =
+                            make_int4((int32_t)(P + off[0]), (int32_t)(P + off[1]), (int32_t)(P + off[2]),
+                                      (int32_t)(P + off[3]));
+                    } else {
+    #pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (i0 + e < cells) start_band[i0 + e] = (int32_t)(P + off[e]);
+                    }
+                }
+                run += __shfl_sync(0xffffffffu, incl, 31);
+            }
+        }
+        __syncthreads();
+        // row starts (before pass 2 moves the offsets on)
+        for (uint32_t r = tid; r < rows; r += kBandNT) a.row_out[r0 + r] = (int32_t)(P + ctr.get(r * L));
+        if (b == a.n_bands - 1u && tid == 0) {
+            a.start[(size_t)L * L] = (int32_t)(P + sh.total);
+            a.row_out[L] = (int32_t)(P + sh.total);
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    // row starts (before pass 2 moves the offsets on)
-    for (uint32_t r = tid; r < rows; r += kBandNT) a.row_out[r0 + r] = (int32_t)(P + ctr.get(r * L));
-    if (b == a.n_bands - 1u && tid == 0) {
-        a.start[(size_t)L * L] = (int32_t)(P + sh.total);
-        a.row_out[L] = (int32_t)(P + sh.total);
-    }
-    __syncthreads();
+    const uint32_t P = sh.prefix;
 
     // the band this CTA takes next (sir_band_kernel reads it after the
     // band): its ticket's latency hides behind pass 2
@@ -520,8 +667,15 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
                 st[u] = 0u;
                 slot[u] = 0u;
                 if (ok[u]) {
-                    st[u] = new_state<kParamKeys>(a, sh.ct, ctr, c, w, ids[u], tl);
-                    slot[u] = P + ctr.take(c);
+                    if constexpr (kNarrow) {
+                        // one atomic gives the slot cursor and the infected count
+                        const uint32_t half = ctr.claim(c);
+                        st[u] = new_state<kParamKeys>(a, sh.ct, KnownK{half >> 12}, c, w, ids[u], tl);
+                        slot[u] = P + sh.rowbase[yo] + (half & 0xFFFu);
+                    } else {
+                        st[u] = new_state<kParamKeys>(a, sh.ct, ctr, c, w, ids[u], tl);
+                        slot[u] = P + ctr.take(c);
+                    }
                 }
                 if (ok[u] && slot[u] >= a.n) {
                     atomicOr(a.err, ERR_OVERFLOW);
@@ -549,13 +703,15 @@ __device__ __forceinline__ void band_body(const BandArgs &a, BandShared &sh, con
         }
     }
     __syncthreads();
+    return true;
 }
 
 // All threads: band b of the step described by `a` (its source-row tables,
 // then band_body with shared-memory or, for very dense bands, global
 // counters).  kTicketAhead: thread 0 draws the ticket of the CTA's next band
-// into sh.band when pass 2 starts.
-template <bool kParamKeys, bool kCoherent, bool kTicketAhead = false>
+// into sh.band when pass 2 starts.  kNarrow: 16-bit shared counters (rows a
+// multiple of 8 cells, at most 8192), else 32-bit ones.
+template <bool kParamKeys, bool kCoherent, bool kTicketAhead = false, bool kNarrow = false>
 __device__ __forceinline__ void process_band(const BandArgs &a, BandShared &sh, uint32_t *band_smem,
                                              uint32_t *wide_slice, uint32_t b, Tally &tl)
 {
@@ -590,11 +746,24 @@ __device__ __forceinline__ void process_band(const BandArgs &a, BandShared &sh, 
         sh.rows[tid] = make_uint4(off + len, beg - off, tab, y);
     }
     __syncthreads();
-    if (M < kPackedLimit || wide_slice == nullptr)
-        band_body<kParamKeys, kCoherent, kTicketAhead>(a, sh, PackedCtr{band_smem}, b, r0, r1, M, tl);
-    else
-        band_body<kParamKeys, kCoherent, kTicketAhead>(a, sh, WideCtr{wide_slice, wide_slice + (size_t)a.H * L}, b, r0, r1,
-                                                       M, tl);
+    if constexpr (kNarrow) {
+        // 16-bit counters; a band that does not fit them is redone with
+        // 32-bit counters in global memory (allocated with the narrow band
+        // shape: the shared array holds only 2 bytes per cell)
+        if (wide_slice == nullptr) {
+            if (tid == 0) atomicOr(a.err, ERR_OVERFLOW);
+            return;
+        }
+        if (!band_body<kParamKeys, kCoherent, kTicketAhead>(a, sh, NarrowCtr{band_smem}, b, r0, r1, M, tl))
+            band_body<kParamKeys, kCoherent, kTicketAhead>(a, sh, WideCtr{wide_slice, wide_slice + (size_t)a.H * L}, b,
+                                                           r0, r1, M, tl);
+    } else {
+        if (M < kPackedLimit || wide_slice == nullptr)
+            band_body<kParamKeys, kCoherent, kTicketAhead>(a, sh, PackedCtr{band_smem}, b, r0, r1, M, tl);
+        else
+            band_body<kParamKeys, kCoherent, kTicketAhead>(a, sh, WideCtr{wide_slice, wide_slice + (size_t)a.H * L}, b,
+                                                           r0, r1, M, tl);
+    }
 }
 
 // All threads: add the block's tally to row[0..3] and clear it.

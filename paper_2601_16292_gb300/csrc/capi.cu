@@ -361,7 +361,9 @@ amb_status check_params(amb_model model, const amb_params *p, uint64_t seed)
         if (!(p->beta >= 0.0 && p->beta <= 1.0) || !(p->gamma >= 0.0 && p->gamma <= 1.0))
             return fail(AMB_EINVAL, "beta and gamma must be in [0, 1]");
         if (p->n_init_infected > p->n) return fail(AMB_EINVAL, "n_init_infected > n");
-        if (p->variant > AMB_SIR_BAND) return fail(AMB_EINVAL, "unknown SIR variant %u", p->variant);
+        if (p->variant > AMB_SIR_BAND16) return fail(AMB_EINVAL, "unknown SIR variant %u", p->variant);
+        if (p->variant == AMB_SIR_BAND16 && (L % 8u != 0 || L > 8192u))
+            return fail(AMB_EINVAL, "16-bit band counters need L a multiple of 8, at most 8192 (L = %u)", L);
     }
     return AMB_OK;
 }

@@ -9,6 +9,8 @@
 
 namespace amb {
 
+// kNarrow: 16-bit shared counters (bands twice as tall), else 32-bit ones
+template <bool kNarrow>
 __global__ void __launch_bounds__(kBandNT, kBandCtasPerSm) sir_band_kernel(const BandArgs a)
 {
     extern __shared__ __align__(16) uint32_t band_smem[];
@@ -27,7 +29,7 @@ __global__ void __launch_bounds__(kBandNT, kBandCtasPerSm) sir_band_kernel(const
     if (tid == 0) sh.band = (uint32_t)atomicAdd(&a.tickets[a.parity], 1ull);
     __syncthreads();
     for (uint32_t b = sh.band; b < a.n_bands; b = sh.band)
-        process_band<true, false, true>(a, sh, band_smem, wide_slice, b, tl);
+        process_band<true, false, true, kNarrow>(a, sh, band_smem, wide_slice, b, tl);
     flush_tally(sh, tl, a.row);
 }
 
@@ -121,15 +123,18 @@ struct BandGeometry {
 // (the whole GPU works on one population); otherwise the fewest bands (many
 // populations share the GPU in a batch).
 static bool band_geometry(uint32_t L, uint32_t grid_max, BandGeometry *g, uint32_t rows_cap = kMaxBandRows,
-                          bool spread = true, uint32_t smem_cap = 0)
+                          bool spread = true, uint32_t smem_cap = 0, bool narrow = false)
 {
+    // bytes of shared counters per cell: 4, or 2 with 16-bit counters
+    const uint32_t cell_bytes = narrow ? 2u : 4u;
     // counters of at most `budget` bytes (kBandSmem, or less for a kernel
     // with more static shared memory); the round-up to groups of four words
     // adds at most 12 bytes, which the kernels' limits leave room for
     const uint32_t budget = smem_cap ? std::min<uint32_t>(smem_cap, kBandSmem) : kBandSmem;
-    if (L < 1 || L > 0xFFFFu || (uint64_t)L * 4u > budget) return false;
+    if (L < 1 || L > 0xFFFFu || (uint64_t)L * cell_bytes > budget) return false;
+    if (narrow && (L % 8u != 0 || L > 8192u)) return false;
     rows_cap = std::max<uint32_t>(1u, std::min<uint32_t>(rows_cap, kMaxBandRows));
-    const uint32_t by_smem = budget / (L * 4u);
+    const uint32_t by_smem = budget / (L * cell_bytes);
     uint32_t H, nb;
     if ((L <= rows_cap || L <= 2u) && L <= by_smem) {
         H = L;
@@ -147,8 +152,22 @@ static bool band_geometry(uint32_t L, uint32_t grid_max, BandGeometry *g, uint32
     }
     g->H = H;
     g->n_bands = nb;
-    g->smem = ((H * L + 3u) & ~3u) * 4u;
+    g->smem = narrow ? ((H * L / 2u + 3u) & ~3u) * 4u : ((H * L + 3u) & ~3u) * 4u;
     return true;
+}
+
+// 16-bit counters for a population: always with AMB_SIR_BAND16, never with
+// AMB_SIR_BAND32; otherwise when they need fewer waves of bands than 32-bit
+// ones and rows hold at most 3,072 agents on average (a row must stay below
+// 4,096; a band where one does not is redone with 32-bit counters).
+static bool choose_narrow(const amb_pop *pop, uint32_t grid_max)
+{
+    const uint32_t L = pop->p.grid_side;
+    BandGeometry g32, g16;
+    if (pop->p.variant == AMB_SIR_BAND32 || !band_geometry(L, grid_max, &g16, kMaxBandRows, true, 0, true))
+        return false;
+    if (pop->p.variant == AMB_SIR_BAND16) return true;
+    return band_geometry(L, grid_max, &g32) && g16.n_bands < g32.n_bands && (uint64_t)pop->p.n <= 3072ull * L;
 }
 
 uint32_t sir_fewest_bands(uint32_t L, uint32_t rows_cap, uint32_t smem_cap)
@@ -172,8 +191,11 @@ amb_status sir_band_init(amb_pop *pop, const int32_t *x, const int32_t *y, const
     const uint64_t C = (uint64_t)L * L;
     const uint32_t grid_max = device_sms() * kBandCtasPerSm;
     BandGeometry g;
-    if (!band_geometry(L, grid_max, &g)) return fail(AMB_EINVAL, "band path does not support L = %u", L);
+    const bool narrow = choose_narrow(pop, grid_max);
+    if (!band_geometry(L, grid_max, &g, kMaxBandRows, true, 0, narrow))
+        return fail(AMB_EINVAL, "band path does not support L = %u", L);
     const uint32_t H = g.H;
+    pop->band_narrow = narrow;
     pop->band_rows = H;
     pop->n_bands = g.n_bands;
     pop->band_grid = std::min<uint32_t>(g.n_bands, grid_max);
@@ -228,11 +250,13 @@ amb_status sir_band_steps(amb_pop *pop, uint32_t k)
     AMB_TRY_CUDA(cudaMemsetAsync(rows, 0, (size_t)k * 4u * sizeof(int64_t), s));
     if (pop->p.n == 0) return AMB_OK;
     const size_t smem = pop->band_smem;
-    AMB_TRY_CUDA(cudaFuncSetAttribute(sir_band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    void (*const kernel)(BandArgs) = pop->band_narrow ? sir_band_kernel<true> : sir_band_kernel<false>;
+    AMB_TRY_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     AMB_TRY(pop->lb.ensure(pop->n_bands, s));
-    // 32-bit per-CTA counters for bands whose source rows hold >= 65536 agents
-    // (allocated on the first step that may need them; batched steps use their own)
-    if (pop->p.n >= kPackedLimit && !pop->band_wide)
+    // 32-bit per-CTA counters for bands whose source rows hold >= 65536 agents,
+    // or that do not fit 16-bit counters (allocated on the first step that may
+    // need them; batched steps use their own)
+    if ((pop->p.n >= kPackedLimit || pop->band_narrow) && !pop->band_wide)
         AMB_TRY(dalloc(&pop->band_wide, (size_t)pop->band_grid * 2u * pop->band_rows * pop->p.grid_side, s));
     BandArgs a;
     round_keys(pop->key0, pop->key1, a.rk0, a.rk1);
@@ -260,7 +284,7 @@ amb_status sir_band_steps(amb_pop *pop, uint32_t k)
         pop->lb.next(&a.parity, &a.epoch);
         a.err = pop->err;
         a.code_tab = nullptr;
-        sir_band_kernel<<<pop->band_grid, kBandNT, smem, s>>>(a);
+        kernel<<<pop->band_grid, kBandNT, smem, s>>>(a);
         AMB_TRY_CUDA(cudaGetLastError());
         pop->cur = out;
         pop->launches += 1;
@@ -311,6 +335,7 @@ amb_status sir_band_regeometry(amb_pop *pop, BandShape shape)
     if (!band_geometry(L, grid_max, &g, shape.rows_cap, shape.spread, shape.smem_cap))
         return fail(AMB_EINVAL, "band path does not support L = %u", L);
     const bool grow = (size_t)g.H * L > (size_t)pop->band_rows * L || std::min<uint32_t>(g.n_bands, grid_max) > pop->band_grid;
+    pop->band_narrow = false;  // batches run 32-bit counters
     pop->band_rows = g.H;
     pop->n_bands = g.n_bands;
     pop->band_grid = std::min<uint32_t>(g.n_bands, grid_max);

@@ -235,6 +235,56 @@ def test_sir_band_dense_rows_use_wide_counters():
     g.close()
 
 
+# ---------------------------------------------- 16-bit band counters --
+@pytest.mark.parametrize("n,L", [(9_000, 8), (30_000, 32), (24_000, 160), (300_000, 704), (1_000_000, 2048),
+                                 (0, 16), (1, 8)])
+def test_sir_band16_geometries(n, L):
+    """16-bit shared counters forced: one band for the whole grid, one-row
+    and several-row bands with a short last band, very dense cells (the
+    8 x 8 grid holds 140 agents per cell: cells reach 16 infected agents and
+    their bands are redone with 32-bit counters)."""
+    g, o = run_pair("sir", n, [1, 2, 7], variant=amb.AMB_SIR_BAND16, seed=3, rep=5, L=L, beta=0.2, gamma=0.05,
+                    n0=max(1, n // 100) if n else 0)
+    assert_index(g, o)
+    assert_occupancy(g, o)
+    assert g.invariants()["ok"] == 1
+    g.close()
+
+
+@pytest.mark.parametrize("n,L", [
+    (40_000, 64),   # ~10 agents per cell: cells with 16 or more infected agents
+    (300_000, 64),  # ~4,700 agents per grid row: rows past the 12-bit offsets
+    (20_000, 8),    # ~310 agents per cell: cells past 255 agents
+])
+def test_sir_band16_overflow_redoes_the_band(n, L):
+    """Bands whose counts do not fit 16-bit counters are redone with 32-bit
+    counters in the same step, and the trajectory stays the oracle's."""
+    g, o = run_pair("sir", n, [1, 2, 5, 12], variant=amb.AMB_SIR_BAND16, seed=9, rep=2, L=L, beta=0.5,
+                    gamma=0.05, n0=n // 20)
+    assert_index(g, o)
+    assert g.invariants()["ok"] == 1
+    g.close()
+
+
+def test_sir_band16_and_band32_agree_long_run():
+    """The same population with 16-bit and with 32-bit band counters, 60
+    steps: identical columns and count series, equal to the oracle."""
+    kw = dict(seed=13, rep=0, L=2400, beta=0.3, gamma=0.02, n0=2000)
+    n = 2_000_000
+    a = amb.Population("sir", n, variant=amb.AMB_SIR_BAND16, **kw)
+    b = amb.Population("sir", n, variant=amb.AMB_SIR_BAND32, **kw)
+    a.step(60)
+    b.step(60)
+    for name in ("x", "y", "state"):
+        assert torch.equal(a.column(name), b.column(name))
+    assert np.array_equal(a.counts(), b.counts())
+    o = oracle.Population("sir", n, **kw).step(60)
+    assert_columns(a, o, "sir")
+    assert np.array_equal(a.counts(), o.counts())
+    a.close()
+    b.close()
+
+
 def test_sir_band_and_generic_agree_long_run():
     kw = dict(seed=12, rep=0, L=400, beta=0.1, gamma=0.03, n0=100)
     a = amb.Population("sir", 96_000, variant=amb.AMB_SIR_BAND, **kw)
@@ -355,7 +405,9 @@ def test_write_column_rejects_out_of_range():
 def test_create_rejects_bad_params():
     for kw in (dict(model="sir", n=10, seed=1, L=0), dict(model="sir", n=10, seed=1, L=10, beta=1.5),
                dict(model="sir", n=10, seed=1, L=10, n0=11), dict(model="walk", n=10, seed=2 ** 32, L=3),
-               dict(model="sir", n=10, seed=1, L=50_000)):
+               dict(model="sir", n=10, seed=1, L=50_000), dict(model="sir", n=10, seed=1, L=12, variant=5),
+               dict(model="sir", n=10, seed=1, L=12, variant=amb.AMB_SIR_BAND16),
+               dict(model="sir", n=10, seed=1, L=8200, variant=amb.AMB_SIR_BAND16)):
         model = kw.pop("model")
         with pytest.raises(amb.AmbError) as e:
             amb.Population(model, **kw)
