@@ -279,12 +279,14 @@ struct NarrowCtr {
                 for (uint32_t e = i; e < words; ++e) w[e] = 0u;
         }
     }
-    // true when the cell's agent or infected count was already 255
+    // no read-back: a count that wraps (256 agents) lowers the band's sum of
+    // agent counts below the number of agents counted, which the scan checks
+    // (a carry out of an infected count needs such a wrap first, and adds at
+    // most one agent where the wrap took 256)
     __device__ __forceinline__ bool add(uint32_t c, bool infected) const
     {
-        const uint32_t sh = (c & 1u) << 4;
-        const uint32_t old = atomicAdd(&w[c >> 1], (infected ? 0x101u : 1u) << sh) >> sh;
-        return (old & 0xFFu) == 0xFFu || (infected && (old & 0xFF00u) == 0xFF00u);
+        atomicAdd(&w[c >> 1], (infected ? 0x101u : 1u) << ((c & 1u) << 4));
+        return false;
     }
     // the cell's half before taking a slot: cursor | infected count << 12
     __device__ __forceinline__ uint32_t claim(uint32_t c) const
@@ -490,12 +492,13 @@ __device__ __forceinline__ bool band_body(const BandArgs &a, BandShared &sh, con
                 const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= (uint32_t)o) incl += t;
             }
-            const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
-            const uint32_t Pb = lookback_wait(a.status, b, a.epoch, T, a.err);
+            // T below the agents counted in pass 1: a count wrapped
+            const uint32_t T = __shfl_sync(0xffffffffu, incl, 31), counted = sh.total;
+            const uint32_t Pb = lookback_wait(a.status, b, a.epoch, counted, a.err);
             if (lane < rows) sh.rowbase[lane] = incl - v;
             if (lane == 0) {
                 sh.prefix = Pb;
-                sh.total = T;
+                if (T != counted) sh.overflow = 1u;
             }
         }
         __syncthreads();
