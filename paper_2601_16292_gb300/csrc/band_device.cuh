@@ -175,6 +175,38 @@ __device__ __forceinline__ T ld_nc(const T *p)
         return __ldg(p);
 }
 
+// L2 eviction hints (single-population steps): the records a step writes are
+// the next step's input and should stay in L2; the cell index start[] and the
+// input records after their last read should leave first.
+__device__ __forceinline__ uint64_t l2_evict_first()
+{
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_last()
+{
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint2 ld_nc_hint(const uint2 *q, uint64_t pol)
+{
+    uint2 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;" : "=r"(v.x), "=r"(v.y) : "l"(q), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_hint(uint2 *q, uint2 v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(q), "r"(v.x), "r"(v.y), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_hint(int4 *q, int4 v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v4.s32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(q), "r"(v.x), "r"(v.y), "r"(v.z),
+                 "r"(v.w), "l"(pol)
+                 : "memory");
+}
+
 // ------------------------------------------------------------- counters ---
 struct PackedCtr {
     uint32_t *w;  // shared memory
@@ -528,8 +560,12 @@ __device__ __forceinline__ bool band_body(const BandArgs &a, BandShared &sh, con
                 if (valid) {
                     *reinterpret_cast<uint2 *>(rw + i) = make_uint2(o0 | (o1 << 16) | ((q.x & 0x0F000F00u) << 4),
                                                                     o2 | (o3 << 16) | ((q.y & 0x0F000F00u) << 4));
-                    *reinterpret_cast<int4 *>(srow + 2u * i) =
+                    const int4 sv =
                         make_int4((int32_t)(base + o0), (int32_t)(base + o1), (int32_t)(base + o2), (int32_t)(base + o3));
+                    if constexpr (kTicketAhead)
+                        st_hint(reinterpret_cast<int4 *>(srow + 2u * i), sv, l2_evict_first());
+                    else
+                        *reinterpret_cast<int4 *>(srow + 2u * i) = sv;
                 }
                 run += __shfl_sync(0xffffffffu, incl, 31);
             }
@@ -649,7 +685,11 @@ __device__ __forceinline__ bool band_body(const BandArgs &a, BandShared &sh, con
                 if (v < M) {
                     while (ri.x <= v) ri = sh.rows[++j];
                     yy[u] = ri.z;
-                    const uint2 rv = ld_nc<kCoherent>(&a.rec_in[v + ri.y]);
+                    uint2 rv;
+                    if constexpr (kTicketAhead && !kCoherent)
+                        rv = ld_nc_hint(&a.rec_in[v + ri.y], l2_evict_first());  // the record's last read
+                    else
+                        rv = ld_nc<kCoherent>(&a.rec_in[v + ri.y]);
                     ids[u] = rv.x;
                     aux[u] = rv.y;
                 }
@@ -691,7 +731,11 @@ __device__ __forceinline__ bool band_body(const BandArgs &a, BandShared &sh, con
 #pragma unroll
             for (int u = 0; u < kU2; ++u) {
                 if (!ok[u]) continue;
-                a.rec_out[slot[u]] = make_uint2(ids[u], pack_record(r[u], st[u], aux[u] & kAuxXMask, L, a.t_rec));
+                const uint2 rec = make_uint2(ids[u], pack_record(r[u], st[u], aux[u] & kAuxXMask, L, a.t_rec));
+                if constexpr (kTicketAhead)
+                    st_hint(&a.rec_out[slot[u]], rec, l2_evict_last());  // the next step's input
+                else
+                    a.rec_out[slot[u]] = rec;
             }
         };
         constexpr uint32_t G = kBandNT * kU2;
