@@ -212,6 +212,7 @@ struct amb_pop {
     cudaEvent_t ev_ready = nullptr, ev_copied = nullptr;
     bool copies_pending = false;
     size_t series_cap = 0;
+    bool series_next_zero = false;  // count row t is known to be zero (the last band step cleared it)
 
     // continuous-space models: float positions, days infected, and the
     // infected agents' positions in cell order (grid of cells wider than r)

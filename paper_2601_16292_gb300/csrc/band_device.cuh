@@ -69,7 +69,8 @@ struct BandArgs {
     uint32_t rk0[10], rk1[10];  // Philox round keys of (k0, k1)
     const uint32_t *t_inf;
     uint32_t K, t_rec;
-    int64_t *row;  // the step's count row
+    int64_t *row;       // the step's count row
+    int64_t *row_next;  // single-population launches: the next step's count row, cleared here (or null)
     unsigned long long *tickets;
     uint32_t parity;
     uint64_t *status;

@@ -549,6 +549,7 @@ amb_status advance(const std::vector<amb_pop *> &pops, const std::vector<uint32_
         AMB_TRY(band_sync_records(p));
         AMB_TRY(ensure_series(p, p->t + k));
         if (k) AMB_TRY_CUDA(cudaMemsetAsync(p->series + (size_t)p->t * 4u, 0, (size_t)k * 4u * sizeof(int64_t), s));
+        p->series_next_zero = false;
     }
     // up to three persistent launches, one after the other, by the shared
     // memory their CTAs need: the SIR jobs (band counters), the small wealth

@@ -188,6 +188,7 @@ amb_status ensure_series(amb_pop *pop, uint64_t rows)
     dfree(pop->series, pop->stream);
     pop->series = ns;
     pop->series_cap = cap;
+    pop->series_next_zero = false;
     return AMB_OK;
 }
 
@@ -526,7 +527,14 @@ amb_status amb_step(amb_pop *pop, uint32_t k)
         st = walk_steps(pop, k);
         pop->index_valid = false;
         break;
-    case AMB_SIR: st = (pop->path == AMB_SIR_BAND) ? sir_band_steps(pop, k) : sir_generic_steps(pop, k); break;
+    case AMB_SIR:
+        if (pop->path == AMB_SIR_BAND) {
+            st = sir_band_steps(pop, k);  // sets series_next_zero
+        } else {
+            st = sir_generic_steps(pop, k);
+            pop->series_next_zero = false;
+        }
+        break;
     case AMB_CWALK:
     case AMB_CSIR: st = cont_steps(pop, k); break;
     }
@@ -545,6 +553,7 @@ amb_status amb_set_step(amb_pop *pop, uint64_t t)
     if (t > pop->t)  // rows of steps that were not run here read as zeros
         AMB_TRY_CUDA(cudaMemsetAsync(pop->series + (size_t)pop->t * 4u, 0, (size_t)(t - pop->t) * 4u * sizeof(int64_t), s));
     pop->t = t;
+    pop->series_next_zero = false;
     pop->conservation_from = t;
     pop->monotone_from = t;
     amb_status st = AMB_OK;

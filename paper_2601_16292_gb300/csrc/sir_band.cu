@@ -18,6 +18,8 @@ __global__ void __launch_bounds__(kBandNT, kBandCtasPerSm) sir_band_kernel(const
     const uint32_t tid = threadIdx.x;
 
     if (blockIdx.x == 0 && tid == 0) a.tickets[a.parity ^ 1u] = 0ull;
+    // the next step's launch adds into its row only after this one ends
+    if (blockIdx.x == 0 && tid < 4 && a.row_next) a.row_next[tid] = 0;
     if (tid < 4) sh.cnt[tid] = 0ull;
     load_code_tables(sh.ct, a.t_inf, a.K);
     Tally tl = {0u, 0u, 0u, 0u};
@@ -246,9 +248,18 @@ amb_status sir_band_init(amb_pop *pop, const int32_t *x, const int32_t *y, const
 amb_status sir_band_steps(amb_pop *pop, uint32_t k)
 {
     cudaStream_t s = pop->stream;
+    // every launch clears the next step's count row, so only the first row
+    // needs clearing here, and not even that after a band step of this
+    // population (one more row of capacity keeps the last launch's next row)
+    AMB_TRY(ensure_series(pop, pop->t + k + 1));
     int64_t *rows = pop->series + (size_t)pop->t * 4u;
-    AMB_TRY_CUDA(cudaMemsetAsync(rows, 0, (size_t)k * 4u * sizeof(int64_t), s));
-    if (pop->p.n == 0) return AMB_OK;
+    if (pop->p.n == 0) {
+        AMB_TRY_CUDA(cudaMemsetAsync(rows, 0, (size_t)(k + 1) * 4u * sizeof(int64_t), s));
+        pop->series_next_zero = true;
+        return AMB_OK;
+    }
+    if (!pop->series_next_zero) AMB_TRY_CUDA(cudaMemsetAsync(rows, 0, 4u * sizeof(int64_t), s));
+    pop->series_next_zero = false;
     const size_t smem = pop->band_smem;
     void (*const kernel)(BandArgs) = pop->band_narrow ? sir_band_kernel<true> : sir_band_kernel<false>;
     AMB_TRY_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -279,6 +290,7 @@ amb_status sir_band_steps(amb_pop *pop, uint32_t k)
         a.K = pop->K;
         a.t_rec = pop->t_rec;
         a.row = rows + (size_t)j * 4u;
+        a.row_next = rows + (size_t)(j + 1) * 4u;
         a.tickets = pop->lb.tickets;
         a.status = pop->lb.status;
         pop->lb.next(&a.parity, &a.epoch);
@@ -289,6 +301,7 @@ amb_status sir_band_steps(amb_pop *pop, uint32_t k)
         pop->cur = out;
         pop->launches += 1;
     }
+    pop->series_next_zero = true;
     return AMB_OK;
 }
 
