@@ -17,19 +17,22 @@ __global__ void __launch_bounds__(kBandNT, kBandCtasPerSm) sir_band_kernel(const
     __shared__ BandShared sh;
     const uint32_t tid = threadIdx.x;
 
+    // Bands are handed out in increasing order by ticket.  A CTA draws the
+    // ticket of its next band during the current band's pass 2; the smallest
+    // unfinished band is always some CTA's current one (all CTAs are
+    // resident), so every look-back ends.  The first ticket is drawn before
+    // the threshold table is loaded, so that its latency overlaps the loads.
+    unsigned long long ticket = 0;
+    if (tid == 0) ticket = atomicAdd(&a.tickets[a.parity], 1ull);
     if (blockIdx.x == 0 && tid == 0) a.tickets[a.parity ^ 1u] = 0ull;
     // the next step's launch adds into its row only after this one ends
     if (blockIdx.x == 0 && tid < 4 && a.row_next) a.row_next[tid] = 0;
     if (tid < 4) sh.cnt[tid] = 0ull;
-    load_code_tables(sh.ct, a.t_inf, a.K);
+    for (uint32_t i = tid; i < 256u; i += kBandNT) sh.ct.tinf[i] = a.t_inf[i < a.K ? i : a.K];
+    if (tid == 0) sh.band = (uint32_t)ticket;
+    __syncthreads();
     Tally tl = {0u, 0u, 0u, 0u};
     uint32_t *wide_slice = a.wide ? a.wide + (size_t)blockIdx.x * 2u * a.H * a.L : nullptr;
-    // Bands are handed out in increasing order by ticket.  A CTA draws the
-    // ticket of its next band during the current band's pass 2; the smallest
-    // unfinished band is always some CTA's current one (all CTAs are
-    // resident), so every look-back ends.
-    if (tid == 0) sh.band = (uint32_t)atomicAdd(&a.tickets[a.parity], 1ull);
-    __syncthreads();
     for (uint32_t b = sh.band; b < a.n_bands; b = sh.band)
         process_band<true, false, true, kNarrow>(a, sh, band_smem, wide_slice, b, tl);
     flush_tally(sh, tl, a.row);
