@@ -148,3 +148,26 @@ def test_injected_creation_failures_on_the_host():
         assert e.value.status == amb.AMB_EINVAL
     finally:
         amb.amb_debug_fail_creates(0)
+
+
+def test_sir_variant_constants_match_header():
+    """The binding's SIR path constants are the header's enum values."""
+    with open(os.path.join(os.path.dirname(__file__), "..", "include", "amb.h")) as f:
+        text = f.read()
+    for name in ("AMB_SIR_AUTO", "AMB_SIR_GENERIC", "AMB_SIR_BAND", "AMB_SIR_BAND32", "AMB_SIR_BAND16"):
+        m = re.search(r"\b%s\s*=\s*(\d+)" % name, text)
+        assert m is not None, name
+        assert int(m.group(1)) == getattr(amb, name), name
+
+
+def test_job_bytes_rejects_bad_band16_grids():
+    """16-bit band counters need rows of a multiple of 8 cells, at most 8192."""
+    for L, ok in ((12, False), (8200, False), (16, True), (8192, True)):
+        job = amb.make_job("sir", 10, seed=1, steps=1, L=L, beta=0.5, gamma=0.1, n0=1)
+        job.params.variant = amb.AMB_SIR_BAND16
+        if ok:
+            amb.amb_job_bytes(job)
+        else:
+            with pytest.raises(amb.AmbError) as e:
+                amb.amb_job_bytes(job)
+            assert e.value.status == amb.AMB_EINVAL
