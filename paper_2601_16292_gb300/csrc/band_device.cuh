@@ -17,9 +17,10 @@
 //   1. reads those records and counts, in shared memory, agents and
 //      start-of-step infected agents per new cell of the band (the cell
 //      histogram and the per-cell infected counts k);
-//   2. scans the band's counts (block-level exclusive scan) and gets the
-//      band's first output slot from its predecessors by decoupled look-back
-//      (bands are handed out in order by an atomic ticket);
+//   2. publishes the number of agents it counted, scans the band's counts
+//      and gets the band's first output slot from its predecessors by
+//      decoupled look-back (bands are handed out in order by an atomic
+//      ticket);
 //   3. writes start[] for its cells and row_start for its rows;
 //   4. reads the records again (now from L2) and, for each agent landing in
 //      the band, applies infection (its infection draw against the threshold
@@ -29,13 +30,17 @@
 //      the record to its new slot.
 // Per-step S / I / R / new-infection counts are warp-aggregated.
 //
-// Counters.  A band whose source rows hold fewer than 65,536 records keeps
-// one 32-bit word per cell in shared memory: the low half is the agent count,
-// then (after the scan) the cell's offset inside the band, then the slot
-// cursor; the high half is the infected count.  No half can overflow because
-// every value is bounded by the band's record count.  A denser band uses two
-// 32-bit counters per cell in a per-CTA slice of global memory instead (same
-// steps, exact for any density).
+// Counters.  32-bit mode: a band whose source rows hold fewer than 65,536
+// records keeps one 32-bit word per cell in shared memory: the low half is
+// the agent count, then (after the scan) the cell's offset inside the band,
+// then the slot cursor; the high half is the infected count.  No half can
+// overflow because every value is bounded by the band's record count.  A
+// denser band uses two 32-bit counters per cell in a per-CTA slice of global
+// memory instead (same steps, exact for any density).  16-bit mode (NarrowCtr
+// below): two bytes per cell, so bands are twice as tall for the same shared
+// memory; the scan runs one warp per band row and offsets are relative to
+// the row; a band whose counts do not fit is redone in the global 32-bit
+// counters.
 //
 // Infection test.  A susceptible agent's record holds the top byte of its
 // infection draw u1 for the step; with k infected agents in its new cell it
