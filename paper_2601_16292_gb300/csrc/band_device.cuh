@@ -738,10 +738,7 @@ __device__ __forceinline__ bool band_body(const BandArgs &a, BandShared &sh, con
             for (int u = 0; u < kU2; ++u) {
                 if (!ok[u]) continue;
                 const uint2 rec = make_uint2(ids[u], pack_record(r[u], st[u], aux[u] & kAuxXMask, L, a.t_rec));
-                if constexpr (kTicketAhead)
-                    st_hint(&a.rec_out[slot[u]], rec, l2_evict_last());  // the next step's input
-                else
-                    a.rec_out[slot[u]] = rec;
+                a.rec_out[slot[u]] = rec;
             }
         };
         constexpr uint32_t G = kBandNT * kU2;
