@@ -181,19 +181,12 @@ __device__ __forceinline__ T ld_nc(const T *p)
         return __ldg(p);
 }
 
-// L2 eviction hints (single-population steps): the records a step writes are
-// the next step's input and should stay in L2; the cell index start[] and the
-// input records after their last read should leave first.
+// L2 eviction hints (single-population steps): the cell index start[] and
+// the input records after their last read leave L2 first.
 __device__ __forceinline__ uint64_t l2_evict_first()
 {
     uint64_t p;
     asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-__device__ __forceinline__ uint64_t l2_evict_last()
-{
-    uint64_t p;
-    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
     return p;
 }
 __device__ __forceinline__ uint2 ld_nc_hint(const uint2 *q, uint64_t pol)
@@ -201,10 +194,6 @@ __device__ __forceinline__ uint2 ld_nc_hint(const uint2 *q, uint64_t pol)
     uint2 v;
     asm volatile("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;" : "=r"(v.x), "=r"(v.y) : "l"(q), "l"(pol));
     return v;
-}
-__device__ __forceinline__ void st_hint(uint2 *q, uint2 v, uint64_t pol)
-{
-    asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(q), "r"(v.x), "r"(v.y), "l"(pol) : "memory");
 }
 __device__ __forceinline__ void st_hint(int4 *q, int4 v, uint64_t pol)
 {
